@@ -1,0 +1,532 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these checks re-types the oracle's own formula: each compares the
+oracle with an identity, a closed form, a special case that reduces to a
+textbook routine (Python's complex arithmetic), a brute-force computation,
+or a published value.  A plausible slip in the oracle (a dropped factor, a
+wrong sign or index, a transposed operand) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2102_01747_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- splitmix64
+def test_splitmix64_published_value(orc):
+    """First output of the public splitmix64 reference from state 0."""
+    for line in open(os.path.join(GOLDEN, "splitmix64.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        state, want = (int(v, 16) for v in line.split())
+        assert orc.splitmix64(state) == want
+
+
+def test_jitter_is_exact_24bit_grid(orc):
+    for pix in range(50):
+        sx, sy = orc.jitter(7, pix, 4, pix % 4)
+        for v in (sx, sy):
+            assert 0.0 <= v < 1.0
+            assert float(v * 2**24).is_integer()
+    # different samples of one pixel differ
+    assert orc.jitter(7, 3, 4, 0) != orc.jitter(7, 3, 4, 1)
+
+
+# --------------------------------------------------------------- quaternions
+def _rand_q(rng, k):
+    return rng.standard_normal((k, 4)) * rng.uniform(0.1, 3.0, (k, 1))
+
+
+def test_quaternion_units(orc):
+    """Hamilton's relations i^2 = j^2 = k^2 = ijk = -1, ij = k, jk = i, ki = j."""
+    one, i, j, k = np.eye(4)
+    assert np.array_equal(orc.qmul(i, i), -one)
+    assert np.array_equal(orc.qmul(j, j), -one)
+    assert np.array_equal(orc.qmul(k, k), -one)
+    assert np.array_equal(orc.qmul(i, j), k)
+    assert np.array_equal(orc.qmul(j, k), i)
+    assert np.array_equal(orc.qmul(k, i), j)
+    assert np.array_equal(orc.qmul(j, i), -k)
+    assert np.array_equal(orc.qmul(orc.qmul(i, j), k), -one)
+
+
+def test_quaternion_norm_multiplicative(orc):
+    """|pq| = |p||q| (the quaternions are a normed division algebra)."""
+    rng = np.random.default_rng(1)
+    P, Q = _rand_q(rng, 20000), _rand_q(rng, 20000)
+    worst64 = worst32 = 0.0
+    for a, b in zip(P, Q):
+        pq = orc.qmul(a, b)
+        want = np.linalg.norm(a) * np.linalg.norm(b)
+        worst64 = max(worst64, abs(np.linalg.norm(pq) - want) / want)
+        if len(P) and worst32 < 1.0:
+            pq32 = orc.qmul(a, b, "f32").astype(np.float64)
+            w32 = np.linalg.norm(a.astype(np.float32)) * np.linalg.norm(b.astype(np.float32))
+            worst32 = max(worst32, abs(np.linalg.norm(pq32) - w32) / w32)
+    assert worst64 < 1e-14
+    assert worst32 < 1e-6
+
+
+def test_quaternion_associative_and_conjugate(orc):
+    rng = np.random.default_rng(2)
+    for a, b, c in zip(_rand_q(rng, 500), _rand_q(rng, 500), _rand_q(rng, 500)):
+        l = orc.qmul(orc.qmul(a, b), c)
+        r = orc.qmul(a, orc.qmul(b, c))
+        assert np.allclose(l, r, rtol=0, atol=1e-13 * np.linalg.norm(l) + 1e-300)
+        conj = a * np.array([1, -1, -1, -1])
+        qq = orc.qmul(a, conj)
+        assert abs(qq[0] - np.dot(a, a)) <= 1e-14 * np.dot(a, a)
+        assert np.all(np.abs(qq[1:]) <= 1e-14 * np.dot(a, a))
+
+
+def test_quaternion_complex_copy_bitwise(orc):
+    """span{1, i} is a copy of C: the product equals Python's complex product."""
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        a = complex(*rng.standard_normal(2))
+        b = complex(*rng.standard_normal(2))
+        q = orc.qmul([a.real, a.imag, 0, 0], [b.real, b.imag, 0, 0])
+        ab = a * b
+        assert q[0] == ab.real and q[1] == ab.imag and q[2] == 0 and q[3] == 0
+
+
+def test_quaternion_power_is_repeated_product(orc):
+    rng = np.random.default_rng(4)
+    for q in _rand_q(rng, 200):
+        q3 = orc.qpow(q, 3)
+        assert np.allclose(q3, orc.qmul(orc.qmul(q, q), q), rtol=1e-15, atol=0)
+        # q commutes with its powers
+        assert np.allclose(orc.qmul(q, orc.qpow(q, 2)), orc.qmul(orc.qpow(q, 2), q),
+                           rtol=0, atol=1e-13 * np.linalg.norm(q) ** 3)
+
+
+# ---------------------------------------------------- White-Nylander power (Eq. 1)
+def test_bulb_power_modulus(orc):
+    """|p^n| = |p|^n for the spherical power formula."""
+    rng = np.random.default_rng(5)
+    for _ in range(3000):
+        v = rng.standard_normal(3) * rng.uniform(0.2, 1.5)
+        n = int(rng.integers(2, 17))
+        r = np.linalg.norm(v)
+        got = np.linalg.norm(orc.bulb_pow(v, n))
+        assert abs(got - r**n) <= 1e-13 * r**n
+
+
+def test_bulb_power_axis_points(orc):
+    """On the polar axis p^n stays on the axis; (0, 0, r)^8 has polar angle
+    8 * pi/2 = 4 pi, i.e. it lands on +y with modulus r^8."""
+    for n in range(2, 12):
+        assert np.allclose(orc.bulb_pow([0.0, 1.3, 0.0], n), [0.0, 1.3**n, 0.0], rtol=1e-14, atol=0)
+    got = orc.bulb_pow([0.0, 0.0, 0.9], 8)
+    assert np.allclose(got, [0.0, 0.9**8, 0.0], rtol=0, atol=1e-14)
+
+
+def test_bulb_power_reduces_to_complex_power(orc):
+    """In the half-plane x = 0, z > 0 the azimuth is 0 and Eq. 1 is the complex
+    power: (0, y, z)^n = (0, Re zeta^n, Im zeta^n) with zeta = y + i z."""
+    rng = np.random.default_rng(6)
+    for _ in range(2000):
+        y = rng.uniform(-1.5, 1.5)
+        z = rng.uniform(1e-3, 1.5)
+        n = int(rng.integers(2, 11))
+        zeta = complex(y, z) ** n
+        got = orc.bulb_pow([0.0, y, z], n)
+        r = abs(complex(y, z))
+        # acos near the pole magnifies the rounding of y/r by 1/sin(polar angle) = r/z
+        tol = 1e-14 * n * r**n * (1.0 + r / z)
+        assert got[0] == 0.0
+        assert abs(got[1] - zeta.real) <= tol
+        assert abs(got[2] - zeta.imag) <= tol
+
+
+def test_bulb_power_f32_close_to_f64(orc):
+    rng = np.random.default_rng(7)
+    for _ in range(500):
+        v = rng.standard_normal(3)
+        v32 = v.astype(np.float32).astype(np.float64)
+        a = orc.bulb_pow(v32, 8)
+        b = orc.bulb_pow(v32, 8, "f32")
+        assert np.allclose(a, b, rtol=0, atol=5e-6 * np.linalg.norm(v32) ** 8)
+
+
+# ------------------------------------------- Julia set restricted to span{1, i}
+def _complex_de(z, c, max_iter, esc2):
+    """The 2D escape-time orbit with its derivative, |f'|^2 carried as in the
+    quaternion DE: returns (d, n_nonescaping, trips, m2)."""
+    dz2, m2, n, trips = 1.0, 0.0, 0, 0
+    for _ in range(max_iter):
+        trips += 1
+        dz2 *= 4.0 * (z.real * z.real + z.imag * z.imag)
+        z = z * z + c
+        m2 = z.real * z.real + z.imag * z.imag
+        if m2 > esc2:
+            break
+        n += 1
+    return 0.25 * math.log(m2) * math.sqrt(m2 / dz2), n, trips, m2
+
+
+def test_julia_complex_subspace_bitwise(orc):
+    """With c and the point in span{1, i}, the quaternion orbit is the complex
+    orbit of z^2 + c (Sec. 1.1): counts, |z|^2 and the DE agree bit for bit."""
+    rng = np.random.default_rng(8)
+    s = W.julia_256(8, 8)
+    for trial in range(5):
+        c = complex(*rng.uniform(-0.8, 0.8, 2))
+        s["c"] = (c.real, c.imag, 0.0, 0.0)
+        pts = np.c_[rng.uniform(-1.6, 1.6, (300, 2)), np.zeros(300)]
+        d, n, tr, m2 = orc.de(s, pts)
+        for j, (x, y, _) in enumerate(pts):
+            want = _complex_de(complex(x, y), c, s["max_iter"], s["escape_r2"])
+            assert (d[j], n[j], tr[j], m2[j]) == want or (math.isnan(d[j]) and math.isnan(want[0]))
+
+
+def test_julia_complex_subspace_float32(orc):
+    """Same reduction at float precision, against numpy float32 complex steps."""
+    rng = np.random.default_rng(9)
+    s = W.julia_256(8, 8)
+    f = np.float32
+    c = complex(-0.2, 0.6)
+    s["c"] = (c.real, c.imag, 0.0, 0.0)
+    cr, ci = f(c.real), f(c.imag)
+    pts = np.c_[rng.uniform(-1.6, 1.6, (300, 2)), np.zeros(300)].astype(np.float32)
+    d, n, tr, m2 = orc.de(s, pts, "f32")
+    for j, (x, y, _) in enumerate(pts):
+        zr, zi, dz2, mm, cnt = f(x), f(y), f(1), f(0), 0
+        for _ in range(s["max_iter"]):
+            dz2 = f(dz2 * f(f(4) * f(f(zr * zr) + f(zi * zi))))
+            zr, zi = f(f(f(zr * zr) - f(zi * zi)) + cr), f(f(f(zr * zi) + f(zi * zr)) + ci)
+            mm = f(f(zr * zr) + f(zi * zi))
+            if mm > f(16):
+                break
+            cnt += 1
+        assert n[j] == cnt and m2[j] == mm
+
+
+def test_julia_rotated_complex_plane(orc):
+    """For general c = (c0, c1, c2, 0), points x + s*u with u = Im c / |Im c| stay in
+    span{1, u}, a copy of C with c -> c0 + i |Im c|: same escape counts and DE."""
+    rng = np.random.default_rng(10)
+    s = W.julia_256(8, 8)
+    agree, total = 0, 0
+    for trial in range(4):
+        cv = np.r_[rng.uniform(-0.6, 0.6, 3), 0.0]
+        s["c"] = tuple(cv)
+        u = cv[1:3] / np.linalg.norm(cv[1:3])
+        cc = complex(cv[0], np.linalg.norm(cv[1:3]))
+        xs = rng.uniform(-1.5, 1.5, 400)
+        ss = rng.uniform(-1.5, 1.5, 400)
+        pts = np.c_[xs, ss * u[0], ss * u[1]]
+        d, n, tr, m2 = orc.de(s, pts)
+        for j in range(len(xs)):
+            want = _complex_de(complex(xs[j], ss[j]), cc, s["max_iter"], s["escape_r2"])
+            total += 1
+            if n[j] == want[1]:
+                agree += 1
+                assert abs(d[j] - want[0]) <= 1e-10 * max(1.0, abs(want[0]))
+    assert agree / total >= 0.995
+
+
+def test_escape_time_2d_matches_complex(orc):
+    rng = np.random.default_rng(11)
+    for _ in range(2000):
+        z = complex(*rng.uniform(-1.6, 1.6, 2))
+        c = complex(-0.2, 0.6)
+        k, w = 0, z
+        for i in range(50):
+            w = w * w + c
+            if w.real * w.real + w.imag * w.imag > 16.0:
+                k = i + 1
+                break
+        else:
+            k = 50
+        assert orc.julia2d_escape(z, c, 50, 16.0) == k
+
+
+def test_cut_face_is_2d_julia_set(orc):
+    """Render-level form of the slice claim (Fig. 1): with c in span{1, i} and the
+    plane z = 0 cutting away the half-space the camera sits in, a pixel shows the
+    cut face exactly where the 2D complex DE at its plane point is below eps."""
+    s = W.julia_256(48, 48)
+    c = complex(-0.2, 0.6)
+    s["c"] = (c.real, c.imag, 0.0, 0.0)
+    s["camera"]["eye"] = (0.0, 0.0, -3.0)
+    s["plane"] = {"n": (0.0, 0.0, -1.0), "o": 0.0}  # keep z >= 0
+    r = orc.render(s, precision="f64")
+    face = (r["flags"] & 2) > 0
+    bad = 0
+    for idx in range(48 * 48):
+        ro, rd = orc.camera_ray(s, idx % 48, idx // 48)
+        t = -ro[2] / rd[2]
+        x, y = ro[0] + t * rd[0], ro[1] + t * rd[1]
+        d2 = _complex_de(complex(x, y), c, s["max_iter"], s["escape_r2"])[0]
+        if (d2 < s["eps"]) != face[idx] and abs(d2 - s["eps"]) > 1e-9:
+            bad += 1
+    assert face.sum() > 100
+    assert bad == 0
+
+
+# ------------------------------------------ DE bracket against brute force (Eq. 2)
+def _grid(N, L):
+    xs = (np.arange(N) + 0.5) / N * 2 * L - L
+    return xs, 2 * L / N
+
+
+def test_de_bracket_2d_julia(orc):
+    """Against the distance to the escape-time set on a 64^2 grid: the DE is a
+    lower bound (Sec. 2 derives |eps| >= G/|grad G|, a safe step) and, for the
+    connected set of z^2 - 0.2 + 0.6i, within the Koebe factor 4 of it."""
+    from scipy.spatial import cKDTree
+
+    c = complex(-0.2, 0.6)
+    z0, k = 0j, 0
+    for k in range(200):
+        z0 = z0 * z0 + c
+    assert abs(z0) < 2  # orbit of 0 bounded: the Julia set is connected
+    xs, delta = _grid(64, 1.6)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    z = X + 1j * Y
+    inside = np.ones(z.shape, bool)
+    for _ in range(64):
+        z = np.where(inside, z * z + c, z)
+        inside &= np.abs(z) ** 2 <= 16
+    tree = cKDTree(np.c_[X[inside], Y[inside]])
+    rng = np.random.default_rng(12)
+    pts = rng.uniform(-1.6, 1.6, (3000, 2))
+    dbf, _ = tree.query(pts)
+    keep = dbf >= 3 * delta
+    pts, dbf = pts[keep], dbf[keep]
+    s = W.julia_256(8, 8)
+    s["c"] = (c.real, c.imag, 0.0, 0.0)
+    d, *_ = orc.de(s, np.c_[pts, np.zeros(len(pts))])
+    ratio = dbf / d
+    assert np.mean(d <= dbf + math.sqrt(2) * delta) >= 0.99
+    assert np.mean(d <= dbf) >= 0.99
+    assert np.mean(dbf <= 4 * d + math.sqrt(2) * delta) >= 0.99
+    assert 1.2 <= np.median(ratio) <= 2.5
+
+
+def _quat_julia_inside(X, Y, Z, c, iters=64):
+    q = np.stack([X, Y, Z, np.zeros_like(X)], 0)
+    inside = np.ones(X.shape, bool)
+    cv = np.array(c)[:, None, None, None]
+    for _ in range(iters):
+        a, b, cc, dd = q
+        q2 = np.stack([a * a - b * b - cc * cc - dd * dd, 2 * a * b, 2 * a * cc, 2 * a * dd], 0) + cv
+        q = np.where(inside[None], q2, q)
+        inside &= (q**2).sum(0) <= 16
+    return inside
+
+
+def _bulb_inside(X, Y, Z, n, iters=64):
+    """Membership by the escape-time definition of Sec. 1.2 with Eq. 1 written in
+    numpy spherical coordinates (polar from +y, azimuth atan2(x, z))."""
+    C = np.stack([X, Y, Z], 0)
+    w = C.copy()
+    inside = np.ones(X.shape, bool)
+    with np.errstate(all="ignore"):
+        for _ in range(iters):
+            r = np.sqrt((w**2).sum(0))
+            th = np.arccos(np.clip(w[1] / np.where(r > 0, r, 1), -1, 1))
+            ph = np.arctan2(w[0], w[2])
+            rn = r**n
+            w2 = np.stack([rn * np.sin(n * th) * np.sin(n * ph), rn * np.cos(n * th),
+                           rn * np.sin(n * th) * np.cos(n * ph)], 0) + C
+            w = np.where(inside[None], w2, w)
+            inside &= (w**2).sum(0) <= 4
+    return inside
+
+
+@pytest.mark.parametrize("kind", ["julia", "bulb"])
+def test_de_lower_bound_3d(orc, kind):
+    """3D bracket on a 48^3 grid: the DE never exceeds the brute-force distance
+    (+ one voxel diagonal).  No theorem gives an upper factor in 3D, so only the
+    lower bound is asserted; the median ratio is kept in a sane range."""
+    from scipy.spatial import cKDTree
+
+    xs, delta = _grid(48, 1.6)
+    X, Y, Z = np.meshgrid(xs, xs, xs, indexing="ij")
+    if kind == "julia":
+        s = W.julia_256(8, 8)
+        inside = _quat_julia_inside(X, Y, Z, s["c"])
+    else:
+        s = W.bulb_1080p(0, 8, 8)
+        inside = _bulb_inside(X, Y, Z, 8)
+    tree = cKDTree(np.c_[X[inside], Y[inside], Z[inside]])
+    rng = np.random.default_rng(13)
+    pts = rng.uniform(-1.6, 1.6, (2500, 3))
+    dbf, _ = tree.query(pts)
+    keep = dbf >= 3 * delta
+    pts, dbf = pts[keep], dbf[keep]
+    d, *_ = orc.de(s, pts)
+    assert np.mean(d <= dbf + math.sqrt(3) * delta) >= 0.99
+    assert 1.1 <= np.median(dbf / d) <= 3.0
+
+
+# ------------------------------------------------ gradient schemes (Eq. 5)
+def test_tetra_gradient_exact_on_affine(orc):
+    """Sum nu_i = 0 and sum (nu_i)_x nu_i = (4, 0, 0) make Eq. 5 exact on affine
+    fields for every h."""
+    rng = np.random.default_rng(14)
+    for _ in range(200):
+        a = rng.standard_normal(3)
+        b = rng.standard_normal()
+        p = rng.standard_normal(3)
+        h = 10 ** rng.uniform(-4, 0)
+        n = orc.normal_field(1, np.r_[a, b], p, orc.NORMAL_TETRA, h)
+        assert np.allclose(n, a / np.linalg.norm(a), rtol=0, atol=1e-9)
+
+
+def test_central_gradient_exact_on_quadratic(orc):
+    rng = np.random.default_rng(15)
+    for _ in range(200):
+        A = rng.standard_normal((3, 3))
+        g = rng.standard_normal(3)
+        p = rng.standard_normal(3)
+        h = 10 ** rng.uniform(-3, 0)
+        n = orc.normal_field(2, np.r_[A.ravel(), g], p, orc.NORMAL_CENTRAL, h)
+        grad = (A + A.T) @ p + g
+        assert np.allclose(n, grad / np.linalg.norm(grad), rtol=0, atol=1e-8)
+
+
+def test_zero_gradient_falls_back_to_view(orc):
+    n = orc.normal_field(1, [0.0, 0.0, 0.0, 1.0], [0.1, 0.2, 0.3], orc.NORMAL_TETRA, 1e-3,
+                         rd=[0.0, 0.6, 0.8])
+    assert np.allclose(n, [0.0, -0.6, -0.8])
+
+
+# ------------------------------------------------------ sphere tracing
+def test_march_exact_sphere(orc):
+    """With an exact SDF the march stops within eps in front of the analytic root."""
+    rng = np.random.default_rng(16)
+    hits = 0
+    for _ in range(500):
+        q = rng.uniform(-1, 1, 3)
+        r = rng.uniform(0.2, 1.0)
+        ro = rng.uniform(-1, 1, 3) + np.array([0, 0, 4.0])
+        rd = q + rng.normal(0, 0.3, 3) - ro
+        rd /= np.linalg.norm(rd)
+        eps = 1e-4
+        hit, t, steps = orc.march_field(0, np.r_[q, r], ro, rd, eps, 50.0, 1000, eps, 0.2)
+        oc = ro - q
+        b = oc @ rd
+        disc = b * b - (oc @ oc - r * r)
+        if disc >= 0 and -b - math.sqrt(disc) > 0:
+            root = -b - math.sqrt(disc)
+            assert hit
+            # stopped in front of the root, at a point closer than eps to the surface
+            assert t <= root + 1e-12
+            assert np.linalg.norm(ro + t * rd - q) - r < eps
+            # the distance along the ray is at most eps / cos(incidence)
+            cosi = -((ro + root * rd - q) / r) @ rd
+            assert root - t <= eps / cosi + 1e-12
+            assert steps >= math.floor((root - 1.0) / 0.2)  # the step clamp bounds progress
+            hits += 1
+        else:
+            assert not hit
+    assert hits > 100
+
+
+def test_march_step_cap_counts_as_hit(orc):
+    """Out of steps inside the interval: the final test of the ray-cast listing
+    (t < tmax) reports a hit at the current t."""
+    hit, t, steps = orc.march_field(0, [0, 0, 0, 0.5], [0, 0, 10.0], [0, 0, -1.0], 0.0, 100.0,
+                                    5, 1e-4, 0.2)
+    assert hit and steps == 5 and abs(t - 1.0) < 1e-12
+
+
+def test_march_miss_past_interval(orc):
+    hit, t, steps = orc.march_field(0, [0, 0, 0, 0.5], [0, 0, 10.0], [0, 0, -1.0], 0.0, 5.0,
+                                    1000, 1e-4, 0.2)
+    assert not hit and t > 5.0 and steps == 25
+
+
+# ------------------------------------------------------ interval (bounds + cut)
+def test_bounds_brute_force(orc):
+    rng = np.random.default_rng(17)
+    s = W.julia_256(8, 8)
+    for trial in range(300):
+        nrm = rng.standard_normal(3)
+        s["plane"] = {"n": tuple(nrm), "o": float(rng.uniform(-0.5, 0.5))} if trial % 3 else None
+        ro = rng.uniform(-3, 3, 3)
+        rd = rng.standard_normal(3)
+        rd /= np.linalg.norm(rd)
+        ok, t0, t1, fp = orc.bounds(s, ro, rd)
+        ts = np.linspace(0, 8, 80001)
+        P = ro[None] + ts[:, None] * rd[None]
+        inside = (np.sum(P * P, 1) <= 4.0) & (ts >= s["eps"])
+        if s["plane"]:
+            inside &= P @ nrm <= s["plane"]["o"]
+        if inside.sum() < 3:
+            if inside.sum() == 0:
+                assert not ok
+            continue
+        assert ok
+        assert abs(ts[inside].min() - t0) <= 2e-4
+        assert abs(ts[inside].max() - t1) <= 2e-4
+        if fp:
+            assert abs((ro + t0 * rd) @ nrm - s["plane"]["o"]) <= 1e-9 * np.linalg.norm(nrm) * 10
+
+
+# ------------------------------------------------------ shading and quantiser
+def test_lambert_special_cases(orc):
+    s = W.julia_256(8, 8)
+    L = np.array(s["light"]["dir"]) / np.linalg.norm(s["light"]["dir"])
+    alb = np.array(s["light"]["albedo"])
+    ka, kd = s["light"]["k_ambient"], s["light"]["k_diffuse"]
+    assert np.allclose(orc.shade(s, L)[:3], alb * (ka + kd), rtol=1e-15)
+    assert np.allclose(orc.shade(s, -L)[:3], alb * ka, rtol=1e-15)
+    perp = np.cross(L, [0, 0, 1.0])
+    perp /= np.linalg.norm(perp)
+    assert np.allclose(orc.shade(s, perp)[:3], alb * ka, atol=1e-15)
+    assert np.allclose(orc.shade(s, L, 0.0)[:3], alb * ka, rtol=1e-15)
+    assert orc.shade(s, L)[3] == 1.0
+
+
+def test_quantizer_round_half_up(orc):
+    for prec in ("f64", "f32"):
+        assert orc.quantize(0.0, prec) == 0
+        assert orc.quantize(-0.3, prec) == 0
+        assert orc.quantize(1.0, prec) == 255
+        assert orc.quantize(7.0, prec) == 255
+        assert orc.quantize(0.5, prec) == 128  # 127.5 rounds up
+        assert orc.quantize(float("nan"), prec) == 0
+        assert orc.quantize(100.0 / 255.0, prec) == 100
+
+
+# ------------------------------------------------------ camera
+def test_camera_geometry(orc):
+    s = W.julia_256(65, 33)
+    ro, rd = orc.camera_ray(s, 32, 16)
+    f = -np.array(s["camera"]["eye"]) / np.linalg.norm(s["camera"]["eye"])
+    assert np.allclose(ro, s["camera"]["eye"]) and np.allclose(rd, f, atol=1e-15)
+    _, a = orc.camera_ray(s, 0, 0)
+    _, b = orc.camera_ray(s, 64, 32)
+    assert np.allclose(a[:2], -b[:2]) and a[1] > 0 and a[0] < 0  # top-left looks up-left
+    # the image plane spans the vertical field of view
+    half = math.radians(s["camera"]["fov_y_deg"]) / 2
+    _, top = orc.camera_ray(s, 32, 0)
+    ang = math.atan2(top[1], -top[2])
+    assert abs(ang - math.atan((1 - 1 / 33) * math.tan(half))) < 1e-12
+
+
+# ------------------------------------------------------ float oracle vs double oracle
+@pytest.mark.parametrize("which", ["julia", "bulb"])
+def test_f32_oracle_close_to_f64(orc, which):
+    """The float twin agrees with the double reference within the render tolerances
+    (hit/miss on >= 99.5% of pixels, depth and colour on >= 99%)."""
+    s = W.julia_256(64, 64) if which == "julia" else W.bulb_1080p(10, 96, 54)
+    a = orc.render(s, precision="f64", threads=4)
+    b = orc.render(s, precision="f32", threads=4)
+    ha, hb = (a["flags"] & 1) > 0, (b["flags"] & 1) > 0
+    assert np.mean(ha == hb) >= 0.995
+    both = ha & hb
+    rel = np.abs(a["depth"][both] - b["depth"][both]) / a["depth"][both]
+    assert np.mean(rel <= 1e-3) >= 0.99
+    ca = np.stack([(a["rgba8"] >> (8 * k)) & 255 for k in range(4)], -1).astype(int)
+    cb = np.stack([(b["rgba8"] >> (8 * k)) & 255 for k in range(4)], -1).astype(int)
+    assert np.mean(np.all(np.abs(ca - cb) <= 3, -1)) >= 0.99
