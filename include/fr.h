@@ -1,0 +1,234 @@
+/*
+ * fr.h -- C ABI of libfr, a GB300 (sm_103a) CUDA renderer for distance-estimated
+ * sphere tracing of the quaternion Julia set and the degree-n Mandelbulb.
+ *
+ * Method (da Silva, Novello, Lopes, Velho, "Real-time rendering of complex
+ * fractals"):
+ *   - quaternion Julia set of f(q) = q^p + c, seen through the 3D slice
+ *     q = (x, y, z, slice_w), optionally cut by a plane            Sec. 1.1, Fig. 1
+ *   - Mandelbulb of f(v) = v^n + c with the White-Nylander power    Sec. 1.2, Eq. 1
+ *   - distance estimate d = 0.5 |f^k| log|f^k| / |(f^k)'| from the orbit and its
+ *     running derivative                                           Eq. 2, Eqs. 3-4,
+ *                                      Listings "Julia Set distance", "Mandelbulb distance"
+ *   - sphere tracing from t = eps in steps of min(d, max_step) inside the
+ *     interval left by a bounding sphere and the cutting plane     Listing "Julia Set ray cast", Sec. 3.1
+ *   - normal = normalised gradient of d, tetrahedral (Eq. 5, Listing "Normal
+ *     calculation") or central differences
+ *   - closest-hit shading: Lambert with one directional light and an optional
+ *     shadow ray (stands in for the Phong closest-hit of Listing "Closest-hit shader")
+ *
+ * Conventions shared by every entry point:
+ *   - Device memory belongs to the caller.  Every pointer in fr_image, the
+ *     gradient and the batch workspace is a device pointer (cudaMalloc or a
+ *     torch CUDA tensor); the parameter structs and the request array are host
+ *     memory, read before the call returns.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  The library allocates no device memory.
+ *   - Parameters are checked on the host first.  A bad argument returns
+ *     FR_EINVAL, launches nothing and leaves a message for fr_last_error().
+ *     A failed launch returns FR_ECUDA.  Results are defined once the stream
+ *     reaches the work.
+ *   - Images are row-major, row 0 at the top, pixel (x, y) at index y*width + x.
+ *     rgba8 packs r | g<<8 | b<<16 | a<<24, each channel round-half-up of
+ *     clamp(value, 0, 1) * 255.  Depth is the ray parameter t of the nearest hit
+ *     along the unit view ray (world units), +inf where no sample hit.
+ *   - With spp > 1 the colour is the mean over the pixel's samples (sub-pixel
+ *     offsets from splitmix64 of (seed << 40) + pixel*spp + sample) and the depth
+ *     the smallest hit t.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FR_API __attribute__((visibility("default")))
+#else
+#define FR_API
+#endif
+
+typedef enum {
+    FR_OK = 0,
+    FR_EINVAL = 1,     /* bad argument; nothing launched                          */
+    FR_ECUDA = 2,      /* a CUDA call failed (message in fr_last_error)           */
+    FR_ETIMEOUT = 3,   /* reserved: no kernel of this library waits on another    */
+    FR_ENOMEM = 4,     /* caller-provided workspace too small                     */
+    FR_ENOTIMPL = 5    /* combination not supported                               */
+} fr_status;
+
+enum { FR_KIND_JULIA = 0, FR_KIND_BULB = 1 };
+enum { FR_NORMAL_TETRA = 0, FR_NORMAL_CENTRAL = 1 };
+
+/* indices into fr_image.stats */
+enum {
+    FR_STAT_PRIMARY_RAYS = 0,  /* camera rays traced (width*height*spp)              */
+    FR_STAT_SHADOW_RAYS = 1,   /* shadow rays cast (one per shaded hit when enabled)  */
+    FR_STAT_PRIMARY_DE = 2,    /* distance-estimator calls of camera-ray marches      */
+    FR_STAT_NORMAL_DE = 3,     /* distance-estimator calls of the normal stencils     */
+    FR_STAT_SHADOW_DE = 4,     /* distance-estimator calls of shadow-ray marches      */
+    FR_STAT_ORBIT_ITERS = 5,   /* orbit loop trips summed over all DE calls           */
+    FR_NSTATS = 6
+};
+
+/* Pinhole camera.  Forward = target - eye, right = forward x up, vertical field
+ * of view fov_y_deg in (0, 180).  One sample per pixel sits at the pixel centre. */
+typedef struct {
+    float eye[3], target[3], up[3];
+    float fov_y_deg;
+    int32_t width, height;   /* >= 1, width*height*spp < 2^31          */
+    int32_t spp;             /* samples per pixel, 1..64               */
+    uint32_t seed;           /* jitter seed (used when spp > 1)        */
+} fr_camera;
+
+/* Directional light with Lambert shading:
+ *   hit:  rgb = albedo * (k_ambient + k_diffuse * max(0, n . L) * visible), a = 1
+ *   miss: rgba = background */
+typedef struct {
+    float dir[3];            /* toward the light; normalised here, must be non-zero */
+    float albedo[3];
+    float k_ambient, k_diffuse;
+    int32_t shadows;         /* 1: one shadow ray per hit, start x + 4 eps n      */
+    float background[4];
+} fr_light;
+
+/* Cutting plane (Sec. 3.1, Fig. 1): points with dot(n, x) > offset are removed.
+ * A ray whose search interval starts on the plane and whose first DE sample is
+ * already below eps hits the cut face; its normal is n / |n|. */
+typedef struct {
+    int32_t enabled;
+    float n[3];              /* non-zero when enabled                  */
+    float offset;
+} fr_plane;
+
+/* Quaternion Julia set, f(q) = q^p + c (Listing "Julia Set distance" with
+ * degree p; the listing itself uses p = 3, the text of Sec. 1.1 p = 2). */
+typedef struct {
+    float c[4];              /* (real, i, j, k)                                   */
+    int32_t p;               /* 2 or 3                                            */
+    float slice_w;           /* k-component of the 3D slice (0 in the listing)    */
+    int32_t max_iter;        /* orbit iteration cap, 1..1024                      */
+    float escape_r2;         /* escape once |q|^2 > escape_r2 (listing: 256)      */
+    float bound_radius;      /* bounding sphere at the origin, > 0                */
+    int32_t max_steps;       /* march step cap, 1..100000 (listing: 1024)         */
+    float eps;               /* hit threshold kPrecis, > 0                        */
+    float max_step;          /* step clamp (listing: 0.2), > 0                    */
+    int32_t normal_mode;     /* FR_NORMAL_TETRA or FR_NORMAL_CENTRAL              */
+    float normal_h;          /* stencil size; 0 = 0.5773*eps (tetra), 1e-4 (central) */
+} fr_julia_params;
+
+/* Mandelbulb, f(v) = v^n + c with the orbit started at w0 = c (Listing
+ * "Mandelbulb distance"; the listing uses n = 8, 4 iterations, |w|^2 > 256). */
+typedef struct {
+    int32_t n;               /* power, 2..16                                      */
+    int32_t max_iter;        /* orbit iteration cap, 1..1024                      */
+    float bailout;           /* escape once |w| > bailout, > 0                    */
+    float bound_radius;
+    int32_t max_steps;
+    float eps;
+    float max_step;
+    int32_t normal_mode;
+    float normal_h;
+} fr_bulb_params;
+
+/* Output buffers (device).  Any may be NULL except that at least one of rgba8,
+ * rgba, depth, saved, stats must be given.  Alignment: rgba and saved 16 bytes,
+ * the others 4 (stats 8). */
+typedef struct {
+    uint32_t *rgba8;             /* width*height packed colour                        */
+    float *rgba;                 /* width*height*4 mean colour before quantisation     */
+    float *depth;                /* width*height nearest hit t, +inf on a miss         */
+    float *saved;                /* width*height*4: hit point x, y, z and flag bits    */
+                                 /* (1 hit, 2 cut face, 4 shadowed) as a float's bits; */
+                                 /* the state fr_render_backward reads                 */
+    unsigned long long *stats;   /* FR_NSTATS counters, ADDED to (zero them first)     */
+} fr_image;
+
+/* One request of a batch.  `kind` selects which parameter block is read. */
+typedef struct {
+    int32_t kind;            /* FR_KIND_JULIA or FR_KIND_BULB */
+    fr_julia_params julia;
+    fr_bulb_params bulb;
+    fr_plane plane;
+    fr_camera camera;
+    fr_light light;
+    fr_image out;
+} fr_request;
+
+/* Launch shapes; the autotuner writes them, every later call reads them. */
+typedef struct {
+    int32_t plain_block;         /* threads per block of the one-ray-per-thread kernel (32..1024, x32) */
+    int32_t plain_unroll;        /* orbit-loop unroll depth: 1, 2 or 4                  */
+    int32_t persist_block;       /* threads per block of the persistent kernel          */
+    int32_t persist_ctas_per_sm; /* resident CTAs per SM; 0 = as many as fit            */
+    int32_t refill_threshold;    /* refill a warp once this many lanes are idle (1..32) */
+    int32_t persist_unroll;      /* orbit-loop unroll depth of the persistent kernel    */
+} fr_tuning;
+
+/* Render one quaternion Julia image with the one-ray-per-thread kernel
+ * (camera ray -> interval -> march -> normal -> shadow -> shade -> store).
+ * plane may be NULL (no cut).  Errors: FR_EINVAL, FR_ECUDA. */
+FR_API fr_status fr_render_julia(const fr_julia_params *params, const fr_plane *plane,
+                                 const fr_camera *camera, const fr_light *light,
+                                 const fr_image *out, void *stream);
+
+/* Same for the Mandelbulb. */
+FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_plane *plane,
+                                      const fr_camera *camera, const fr_light *light,
+                                      const fr_image *out, void *stream);
+
+/* Device workspace a batch of n_reqs requests needs (bytes, 256-aligned start). */
+FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs);
+
+/* Render n_reqs requests (mixed kinds and sizes) in one persistent launch: CTAs
+ * stay resident and each warp pulls pixels from one queue over all requests,
+ * refilling idle lanes as rays finish.  The request table travels in the
+ * kernel's parameters (staged into shared memory by every CTA), so the call is
+ * a memset of the queue heads plus one kernel launch per 64 requests, with no
+ * host synchronisation and no copy: it can be captured into a CUDA graph and
+ * replayed.  `workspace` (device, >= fr_batch_workspace_bytes(n_reqs) bytes,
+ * 256-byte aligned) holds the queue heads and is overwritten; two batches in
+ * flight at once need two workspaces.  reqs is host memory.
+ * 1 <= n_reqs <= 4096.  Errors: FR_EINVAL, FR_ENOMEM (workspace too small),
+ * FR_ECUDA. */
+FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *workspace,
+                                 size_t ws_bytes, void *stream);
+
+/* Vector-Jacobian product of a Julia render (spp = 1) by implicit
+ * differentiation at the hit point: for surface hits
+ *     dt/dtheta = -(dd/dtheta) / (grad_x d . rd),
+ * the normal's dependence through the stencil taps, Lambert's through n and L;
+ * cut-face hits through t = (offset - n.ro)/(n.rd) and the normal n/|n|.
+ * The orbit is recomputed from the hit point saved by the forward call (same
+ * parameters, out.saved given).  Escape counts, hit status and shadow
+ * visibility are held fixed.
+ *   saved    width*height*4 floats from the forward call (device)
+ *   d_rgba   width*height*4 cotangent of fr_image.rgba (device; alpha ignored)
+ *   d_depth  width*height cotangent of the depth (device, may be NULL; miss
+ *            pixels ignored)
+ *   grad     11 floats (device), ADDED to: dc[4], dplane_n[3], dplane_offset,
+ *            dlight_dir[3]
+ * Errors: FR_EINVAL (spp != 1, NULL buffers, bad parameters), FR_ECUDA. */
+FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,
+                                    const fr_camera *camera, const fr_light *light,
+                                    const float *saved, const float *d_rgba, const float *d_depth,
+                                    float *grad, void *stream);
+
+/* Read / replace the process-wide launch shapes (checked; FR_EINVAL if out of range). */
+FR_API fr_status fr_get_tuning(fr_tuning *out);
+FR_API fr_status fr_set_tuning(const fr_tuning *t);
+
+/* Message of the calling thread's last failure ("" if none). */
+FR_API const char *fr_last_error(void);
+
+/* ABI version of this header (increments on any layout change). */
+FR_API int32_t fr_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,286 @@
+// fr_api.cu -- the C ABI of include/fr.h: argument checks on the host, the
+// resolution of the public structs into DevReq, launch-shape selection and
+// error reporting.  No device memory is allocated here.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/fr.h"
+#include "fr_launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+fr_status fail(fr_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+std::mutex g_tuning_mu;
+fr_tuning g_tuning = {128, 1, 256, 0, 8, 1};
+
+fr_tuning tuning()
+{
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    return g_tuning;
+}
+
+bool finite_n(const float *v, int n)
+{
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+struct F3 {
+    float x, y, z;
+};
+F3 f3(const float *v) { return {v[0], v[1], v[2]}; }
+F3 sub(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+F3 cross(F3 a, F3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+float dot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+float4 f4(F3 a, float w = 0.0f) { return make_float4(a.x, a.y, a.z, w); }
+
+// normalise in float; false if the length is zero or not finite
+bool normalize(F3 &a)
+{
+    float l = std::sqrt(dot(a, a));
+    if (!(l > 0.0f) || !std::isfinite(l)) return false;
+    a = {a.x / l, a.y / l, a.z / l};
+    return true;
+}
+
+fr_status resolve_march(fr::DevReq &R, int max_iter, float bound_radius, int max_steps, float eps,
+                        float max_step, int normal_mode, float normal_h)
+{
+    if (max_iter < 1 || max_iter > 1024) return fail(FR_EINVAL, "max_iter %d outside 1..1024", max_iter);
+    if (!(bound_radius > 0.0f) || !std::isfinite(bound_radius))
+        return fail(FR_EINVAL, "bound_radius must be positive and finite");
+    if (max_steps < 1 || max_steps > 100000)
+        return fail(FR_EINVAL, "max_steps %d outside 1..100000", max_steps);
+    if (!(eps > 0.0f) || !std::isfinite(eps)) return fail(FR_EINVAL, "eps must be positive and finite");
+    if (!(max_step > 0.0f) || !std::isfinite(max_step))
+        return fail(FR_EINVAL, "max_step must be positive and finite");
+    if (normal_mode != FR_NORMAL_TETRA && normal_mode != FR_NORMAL_CENTRAL)
+        return fail(FR_EINVAL, "normal_mode %d unknown", normal_mode);
+    if (!(normal_h >= 0.0f) || !std::isfinite(normal_h))
+        return fail(FR_EINVAL, "normal_h must be >= 0 and finite");
+    R.max_iter = max_iter;
+    R.bound_r2 = bound_radius * bound_radius;
+    R.max_steps = max_steps;
+    R.eps = eps;
+    R.max_step = max_step;
+    R.normal_mode = normal_mode;
+    // default stencil: the listing's 0.5773 * kPrecis (|h nu| = eps) or 1e-4
+    R.normal_h = normal_h > 0.0f ? normal_h : (normal_mode == FR_NORMAL_TETRA ? 0.5773f * eps : 1e-4f);
+    R.shadow_off = 4.0f * eps;
+    return FR_OK;
+}
+
+fr_status resolve_julia(fr::DevReq &R, const fr_julia_params *P)
+{
+    if (!P) return fail(FR_EINVAL, "julia params is NULL");
+    if (P->p != 2 && P->p != 3) return fail(FR_EINVAL, "julia degree p=%d (2 or 3 supported)", P->p);
+    if (!finite_n(P->c, 4) || !std::isfinite(P->slice_w)) return fail(FR_EINVAL, "julia c / slice_w not finite");
+    if (!(P->escape_r2 > 0.0f) || !std::isfinite(P->escape_r2))
+        return fail(FR_EINVAL, "escape_r2 must be positive and finite");
+    R.kind = FR_KIND_JULIA;
+    R.c = make_float4(P->c[0], P->c[1], P->c[2], P->c[3]);
+    R.power = P->p;
+    R.slice_w = P->slice_w;
+    R.esc2 = P->escape_r2;
+    return resolve_march(R, P->max_iter, P->bound_radius, P->max_steps, P->eps, P->max_step,
+                         P->normal_mode, P->normal_h);
+}
+
+fr_status resolve_bulb(fr::DevReq &R, const fr_bulb_params *P)
+{
+    if (!P) return fail(FR_EINVAL, "mandelbulb params is NULL");
+    if (P->n < 2 || P->n > 16) return fail(FR_EINVAL, "mandelbulb power n=%d outside 2..16", P->n);
+    if (!(P->bailout > 0.0f) || !std::isfinite(P->bailout))
+        return fail(FR_EINVAL, "bailout must be positive and finite");
+    R.kind = FR_KIND_BULB;
+    R.c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    R.power = P->n;
+    R.slice_w = 0.0f;
+    R.esc2 = P->bailout * P->bailout;
+    return resolve_march(R, P->max_iter, P->bound_radius, P->max_steps, P->eps, P->max_step,
+                         P->normal_mode, P->normal_h);
+}
+
+fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam, const fr_light *li,
+                         const fr_image *out)
+{
+    if (!cam) return fail(FR_EINVAL, "camera is NULL");
+    if (!li) return fail(FR_EINVAL, "light is NULL");
+    if (!out) return fail(FR_EINVAL, "image is NULL");
+    if (cam->width < 1 || cam->height < 1) return fail(FR_EINVAL, "image %dx%d is empty", cam->width, cam->height);
+    if (cam->spp < 1 || cam->spp > 64) return fail(FR_EINVAL, "spp %d outside 1..64", cam->spp);
+    if ((long long)cam->width * cam->height * cam->spp >= (1LL << 31))
+        return fail(FR_EINVAL, "width*height*spp must stay below 2^31");
+    if (!finite_n(cam->eye, 3) || !finite_n(cam->target, 3) || !finite_n(cam->up, 3))
+        return fail(FR_EINVAL, "camera vectors not finite");
+    if (!(cam->fov_y_deg > 0.0f && cam->fov_y_deg < 180.0f))
+        return fail(FR_EINVAL, "fov_y_deg %g outside (0, 180)", (double)cam->fov_y_deg);
+    F3 fwd = sub(f3(cam->target), f3(cam->eye));
+    if (!normalize(fwd)) return fail(FR_EINVAL, "camera eye equals target");
+    F3 right = cross(fwd, f3(cam->up));
+    if (!normalize(right)) return fail(FR_EINVAL, "camera up is parallel to the view direction");
+    F3 up = cross(right, fwd);
+    const float th = std::tan(0.5f * cam->fov_y_deg * 0.017453292519943295f);
+    R.eye = f4(f3(cam->eye));
+    R.fwd = f4(fwd);
+    R.right = f4(right);
+    R.up = f4(up);
+    R.th = th;
+    R.th_aspect = th * ((float)cam->width / (float)cam->height);
+    R.inv_w = 1.0f / (float)cam->width;
+    R.inv_h = 1.0f / (float)cam->height;
+    R.width = cam->width;
+    R.height = cam->height;
+    R.tiles_x = (cam->width + fr::kTileW - 1) / fr::kTileW;
+    R.spp = cam->spp;
+    R.seed = cam->seed;
+    const long long tiles_y = (cam->height + fr::kTileH - 1) / fr::kTileH;
+    R.n_units = (long long)R.tiles_x * tiles_y * 32;
+    R.unit_begin = 0;
+
+    if (!finite_n(li->dir, 3) || !finite_n(li->albedo, 3) || !finite_n(li->background, 4) ||
+        !std::isfinite(li->k_ambient) || !std::isfinite(li->k_diffuse))
+        return fail(FR_EINVAL, "light values not finite");
+    F3 L = f3(li->dir);
+    if (!normalize(L)) return fail(FR_EINVAL, "light direction is zero");
+    R.light = f4(L);
+    R.albedo = make_float4(li->albedo[0], li->albedo[1], li->albedo[2], 0.0f);
+    R.ka = li->k_ambient;
+    R.kd = li->k_diffuse;
+    R.shadows = li->shadows ? 1 : 0;
+    R.bg = make_float4(li->background[0], li->background[1], li->background[2], li->background[3]);
+
+    R.plane_on = (pl && pl->enabled) ? 1 : 0;
+    R.plane = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    R.plane_hat = R.plane;
+    if (R.plane_on) {
+        if (!finite_n(pl->n, 3) || !std::isfinite(pl->offset)) return fail(FR_EINVAL, "plane not finite");
+        F3 n = f3(pl->n);
+        if (!normalize(n)) return fail(FR_EINVAL, "plane normal is zero");
+        R.plane = make_float4(pl->n[0], pl->n[1], pl->n[2], pl->offset);
+        R.plane_hat = f4(n);
+    }
+
+    if (!out->rgba8 && !out->rgba && !out->depth && !out->saved && !out->stats)
+        return fail(FR_EINVAL, "image has no output buffer");
+    if (!aligned(out->rgba8, 4) || !aligned(out->depth, 4) || !aligned(out->rgba, 16) ||
+        !aligned(out->saved, 16) || !aligned(out->stats, 8))
+        return fail(FR_EINVAL, "output buffer misaligned (rgba/saved 16 B, rgba8/depth 4 B, stats 8 B)");
+    R.rgba8 = out->rgba8;
+    R.rgba = reinterpret_cast<float4 *>(out->rgba);
+    R.depth = out->depth;
+    R.saved = reinterpret_cast<float4 *>(out->saved);
+    R.stats = out->stats;
+    return FR_OK;
+}
+
+fr_status launched(cudaError_t e)
+{
+    if (e != cudaSuccess) return fail(FR_ECUDA, "CUDA launch failed: %s", cudaGetErrorString(e));
+    g_err.clear();
+    return FR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+FR_API int32_t fr_abi_version(void) { return 1; }
+
+FR_API const char *fr_last_error(void) { return g_err.c_str(); }
+
+FR_API fr_status fr_get_tuning(fr_tuning *out)
+{
+    if (!out) return fail(FR_EINVAL, "tuning is NULL");
+    *out = tuning();
+    return FR_OK;
+}
+
+FR_API fr_status fr_set_tuning(const fr_tuning *t)
+{
+    if (!t) return fail(FR_EINVAL, "tuning is NULL");
+    auto block_ok = [](int b) { return b >= 32 && b <= 256 && b % 32 == 0; };
+    auto unroll_ok = [](int u) { return u == 1 || u == 2 || u == 4; };
+    if (!block_ok(t->plain_block) || !block_ok(t->persist_block))
+        return fail(FR_EINVAL, "block sizes must be multiples of 32 in 32..256");
+    if (!unroll_ok(t->plain_unroll) || !unroll_ok(t->persist_unroll))
+        return fail(FR_EINVAL, "unroll depth must be 1, 2 or 4");
+    if (t->persist_ctas_per_sm < 0 || t->persist_ctas_per_sm > 32)
+        return fail(FR_EINVAL, "persist_ctas_per_sm outside 0..32");
+    if (t->refill_threshold < 1 || t->refill_threshold > 32)
+        return fail(FR_EINVAL, "refill_threshold outside 1..32");
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    g_tuning = *t;
+    return FR_OK;
+}
+
+FR_API fr_status fr_render_julia(const fr_julia_params *params, const fr_plane *plane,
+                                 const fr_camera *camera, const fr_light *light, const fr_image *out,
+                                 void *stream)
+{
+    fr::DevReq R;
+    std::memset(&R, 0, sizeof R);
+    fr_status st = resolve_julia(R, params);
+    if (st != FR_OK) return st;
+    if ((st = resolve_common(R, plane, camera, light, out)) != FR_OK) return st;
+    const fr_tuning tu = tuning();
+    return launched(fr::launch_plain(R, tu.plain_block, tu.plain_unroll, out->stats != nullptr,
+                                     (cudaStream_t)stream));
+}
+
+FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_plane *plane,
+                                      const fr_camera *camera, const fr_light *light,
+                                      const fr_image *out, void *stream)
+{
+    fr::DevReq R;
+    std::memset(&R, 0, sizeof R);
+    fr_status st = resolve_bulb(R, params);
+    if (st != FR_OK) return st;
+    if ((st = resolve_common(R, plane, camera, light, out)) != FR_OK) return st;
+    const fr_tuning tu = tuning();
+    return launched(fr::launch_plain(R, tu.plain_block, tu.plain_unroll, out->stats != nullptr,
+                                     (cudaStream_t)stream));
+}
+
+FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs)
+{
+    (void)n_reqs;
+    return 0;
+}
+
+FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *workspace,
+                                 size_t ws_bytes, void *stream)
+{
+    (void)reqs; (void)n_reqs; (void)workspace; (void)ws_bytes; (void)stream;
+    return fail(FR_ENOTIMPL, "fr_render_batch not built yet");
+}
+
+FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,
+                                    const fr_camera *camera, const fr_light *light, const float *saved,
+                                    const float *d_rgba, const float *d_depth, float *grad, void *stream)
+{
+    (void)params; (void)plane; (void)camera; (void)light; (void)saved; (void)d_rgba; (void)d_depth;
+    (void)grad; (void)stream;
+    return fail(FR_ENOTIMPL, "fr_render_backward not built yet");
+}
+
+}  // extern "C"

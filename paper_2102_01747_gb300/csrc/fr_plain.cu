@@ -1,0 +1,50 @@
+// fr_plain.cu -- one ray per thread.  A warp owns an 8 x 4 tile of pixels (so
+// its 32 rays start close together and diverge late); each thread runs its
+// pixel's samples start to finish.  The request rides in the kernel's
+// parameter space (__grid_constant__), read warp-uniformly from the constant
+// bank.
+#include "fr_launch.h"
+#include "fr_trace.cuh"
+
+namespace fr {
+
+template <int KIND, int U, bool COUNT>
+__global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevReq R)
+{
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tile = gtid >> 5;
+    const int lane = threadIdx.x & 31;
+    const int px = (int)(tile % R.tiles_x) * kTileW + (lane & (kTileW - 1));
+    const int py = (int)(tile / R.tiles_x) * kTileH + (lane / kTileW);
+    Counters cnt;
+    if (COUNT)
+        for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
+    if (px < R.width && py < R.height) render_pixel<KIND, U, COUNT>(R, px, py, cnt);
+    if (COUNT) flush_counters(cnt, R.stats);
+}
+
+template <int KIND, int U, bool COUNT>
+static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
+{
+    const long long tiles_y = (R.height + kTileH - 1) / kTileH;
+    const long long threads = (long long)R.tiles_x * tiles_y * 32;
+    const long long grid = (threads + block - 1) / block;
+    plain_kernel<KIND, U, COUNT><<<(unsigned)grid, block, 0, s>>>(R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s)
+{
+    if (count) return R.kind == 0 ? launch_plain_t<0, 1, true>(R, block, s)
+                                  : launch_plain_t<1, 1, true>(R, block, s);
+    if (R.kind == 0) {
+        if (unroll == 4) return launch_plain_t<0, 4, false>(R, block, s);
+        if (unroll == 2) return launch_plain_t<0, 2, false>(R, block, s);
+        return launch_plain_t<0, 1, false>(R, block, s);
+    }
+    if (unroll == 4) return launch_plain_t<1, 4, false>(R, block, s);
+    if (unroll == 2) return launch_plain_t<1, 2, false>(R, block, s);
+    return launch_plain_t<1, 1, false>(R, block, s);
+}
+
+}  // namespace fr

@@ -1,0 +1,151 @@
+// fr_trace.cuh -- per-ray stages built on fr_device.cuh: the march loop, the
+// normal stencils, one traced sample (interval -> march -> normal -> shadow ->
+// shade) and one pixel (samples -> mean colour, nearest depth -> store).
+#pragma once
+
+#include "fr_device.cuh"
+
+namespace fr {
+
+// Sphere tracing (Listing "Julia Set ray cast"): from t0, d = DE(ro + t rd);
+// d < eps -> hit; t += min(d, max_step); t > t1 -> miss; running out of steps
+// inside the interval is reported as a hit at the current t.
+template <int KIND, int U, bool COUNT>
+__device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, float t0, float t1,
+                                      float &t_out, int &steps_out, Counters &cnt, int slot)
+{
+    float t = t0;
+    int steps = 0;
+    bool hit = true;
+    for (int i = 0; i < R.max_steps; i++) {
+        int trips;
+        float d = de<KIND, U>(R, along(ro, rd, t), trips);
+        steps++;
+        if (COUNT) cnt.v[kStatOrbit] += trips;
+        if (d < R.eps) break;
+        t += (d < R.max_step) ? d : R.max_step;
+        if (t > t1) {
+            hit = false;
+            break;
+        }
+    }
+    if (COUNT) cnt.v[slot] += steps;
+    t_out = t;
+    steps_out = steps;
+    return hit;
+}
+
+// Normal = normalised gradient of the DE at x.  Tetrahedral stencil (Eq. 5):
+// g = sum_k (h nu_k) d(x + h nu_k) with nu = (1,-1,-1), (-1,-1,1), (-1,1,-1),
+// (1,1,1); central: g_j = d(x + h e_j) - d(x - h e_j).  A zero or non-finite
+// gradient gives -rd.
+template <int KIND, int U, bool COUNT>
+__device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd, Counters &cnt)
+{
+    const float h = R.normal_h;
+    float3 g;
+    int tr0, tr1, tr2, tr3;
+    if (R.normal_mode == 0) {
+        float d0 = de<KIND, U>(R, v3(x.x + h, x.y - h, x.z - h), tr0);
+        float d1 = de<KIND, U>(R, v3(x.x - h, x.y - h, x.z + h), tr1);
+        float d2 = de<KIND, U>(R, v3(x.x - h, x.y + h, x.z - h), tr2);
+        float d3 = de<KIND, U>(R, v3(x.x + h, x.y + h, x.z + h), tr3);
+        g = v3(h * (d0 - d1 - d2 + d3), h * (-d0 - d1 + d2 + d3), h * (-d0 + d1 - d2 + d3));
+        if (COUNT) {
+            cnt.v[kStatNormalDE] += 4;
+            cnt.v[kStatOrbit] += tr0 + tr1 + tr2 + tr3;
+        }
+    } else {
+        int tr4, tr5;
+        float dxp = de<KIND, U>(R, v3(x.x + h, x.y, x.z), tr0);
+        float dxm = de<KIND, U>(R, v3(x.x - h, x.y, x.z), tr1);
+        float dyp = de<KIND, U>(R, v3(x.x, x.y + h, x.z), tr2);
+        float dym = de<KIND, U>(R, v3(x.x, x.y - h, x.z), tr3);
+        float dzp = de<KIND, U>(R, v3(x.x, x.y, x.z + h), tr4);
+        float dzm = de<KIND, U>(R, v3(x.x, x.y, x.z - h), tr5);
+        g = v3(dxp - dxm, dyp - dym, dzp - dzm);
+        if (COUNT) {
+            cnt.v[kStatNormalDE] += 6;
+            cnt.v[kStatOrbit] += tr0 + tr1 + tr2 + tr3 + tr4 + tr5;
+        }
+    }
+    float l = sqrtf(dot3(g, g));
+    if (!(l > 0.0f) || !isfinite(l)) return rd * -1.0f;
+    return v3(g.x / l, g.y / l, g.z / l);
+}
+
+// One camera sample: interval, march, normal (the plane's for a cut-face hit:
+// interval starts on the plane and the first DE sample is already inside),
+// optional shadow ray from x + 4 eps n toward the light, Lambert shading.
+template <int KIND, int U, bool COUNT>
+__device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float3 rd, float &t_hit,
+                                               uint32_t &flags, float3 &xhit, Counters &cnt)
+{
+    flags = 0;
+    t_hit = __int_as_float(0x7f800000);
+    float t0, t1, t;
+    bool fp;
+    int steps;
+    if (!bounds(R, ro, rd, t0, t1, fp)) return R.bg;
+    if (!march<KIND, U, COUNT>(R, ro, rd, t0, t1, t, steps, cnt, kStatPrimaryDE)) return R.bg;
+    float3 x = along(ro, rd, t);
+    float3 n;
+    uint32_t fl = kFlagHit;
+    if (fp && steps == 1) {
+        n = v3(R.plane_hat);
+        fl |= kFlagFace;
+    } else {
+        n = normal_at<KIND, U, COUNT>(R, x, rd, cnt);
+    }
+    float vis = 1.0f;
+    if (R.shadows) {
+        float3 L = v3(R.light);
+        float3 so = x + n * R.shadow_off;
+        float s0, s1, ts;
+        bool sfp;
+        int ss;
+        if (COUNT) cnt.v[kStatShadowRays] += 1;
+        if (bounds(R, so, L, s0, s1, sfp) &&
+            march<KIND, U, COUNT>(R, so, L, s0, s1, ts, ss, cnt, kStatShadowDE)) {
+            vis = 0.0f;
+            fl |= kFlagShadow;
+        }
+    }
+    t_hit = t;
+    flags = fl;
+    xhit = x;
+    return shade(R, n, vis);
+}
+
+// One pixel: spp samples, mean colour, nearest hit depth, hit point of the
+// nearest hit, OR of the flags; then the stores.
+template <int KIND, int U, bool COUNT>
+__device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Counters &cnt)
+{
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float dmin = __int_as_float(0x7f800000);
+    float3 xh = v3(0.0f, 0.0f, 0.0f);
+    uint32_t fl = 0;
+    for (int s = 0; s < R.spp; s++) {
+        float3 ro, rd, x;
+        float t;
+        uint32_t f;
+        camera_ray(R, px, py, s, ro, rd);
+        if (COUNT) cnt.v[kStatPrimaryRays] += 1;
+        float4 c = trace_sample<KIND, U, COUNT>(R, ro, rd, t, f, x, cnt);
+        acc.x += c.x;
+        acc.y += c.y;
+        acc.z += c.z;
+        acc.w += c.w;
+        if ((f & kFlagHit) && t < dmin) {
+            dmin = t;
+            xh = x;
+        }
+        fl |= f;
+    }
+    const float fs = (float)R.spp;
+    acc = make_float4(acc.x / fs, acc.y / fs, acc.z / fs, acc.w / fs);
+    store_pixel(R, px, py, acc, dmin, xh, fl);
+}
+
+}  // namespace fr

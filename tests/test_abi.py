@@ -1,0 +1,165 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports every
+entry point include/fr.h declares, its ctypes mirror has the C layout, and bad
+arguments are refused on the host (FR_EINVAL) before anything is launched.
+
+Every refused call below leaves all output pointers NULL, so even a missing
+check could not reach a kernel: the "no output buffer" check would still
+refuse it.  The tests look at the message to see which check fired."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2102_01747_gb300 import build as B
+from paper_2102_01747_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fr.h")
+
+
+@pytest.fixture(scope="module")
+def F():
+    B.build()
+    from paper_2102_01747_gb300 import _ffi
+
+    _ffi.load()
+    return _ffi
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"FR_API\s+[\w\s\*]+?\b(fr_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(F):
+    names = declared_functions()
+    assert len(names) >= 9
+    lib = ctypes.CDLL(B.LIB)
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in F.SIGNATURES, "binding lacks " + n
+    assert F.fr_abi_version() == 1
+
+
+def test_struct_layout_matches_header(F):
+    """Compile a probe against fr.h with gcc and compare sizes and offsets."""
+    structs = ["fr_camera", "fr_light", "fr_plane", "fr_julia_params", "fr_bulb_params",
+               "fr_image", "fr_request", "fr_tuning"]
+    fields = {"fr_request": ["julia", "bulb", "plane", "camera", "light", "out"],
+              "fr_camera": ["fov_y_deg", "seed"], "fr_light": ["shadows", "background"],
+              "fr_image": ["stats"]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fr.h"', "int main(void){"]
+    for s in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
+        for f in fields.get(s, []):
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    lines.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "probe.c")
+        open(c, "w").write("\n".join(lines))
+        exe = os.path.join(d, "probe")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    got = dict(l.split() for l in out.strip().splitlines())
+    for s in structs:
+        assert int(got[s]) == ctypes.sizeof(getattr(F, s)), s
+        for f in fields.get(s, []):
+            assert int(got[s + "." + f]) == getattr(getattr(F, s), f).offset, s + "." + f
+
+
+def _structs(scene):
+    from paper_2102_01747_gb300 import api
+
+    return (api.julia_params(scene) if scene["kind"] == "julia" else api.bulb_params(scene),
+            api.plane_struct(scene), api.camera_struct(scene), api.light_struct(scene))
+
+
+def _call(F, scene, img=None):
+    p, pl, cam, li = _structs(scene)
+    img = img if img is not None else F.fr_image()
+    fn = F.fr_render_julia if scene["kind"] == "julia" else F.fr_render_mandelbulb
+    return fn(p, pl, cam, li, img, None), F.fr_last_error()
+
+
+@pytest.mark.parametrize("mutate, needle", [
+    (lambda s: s.update(p=5), "degree"),
+    (lambda s: s.update(max_iter=0), "max_iter"),
+    (lambda s: s.update(eps=-1.0), "eps"),
+    (lambda s: s.update(max_step=0.0), "max_step"),
+    (lambda s: s.update(max_steps=0), "max_steps"),
+    (lambda s: s.update(escape_r2=0.0), "escape_r2"),
+    (lambda s: s.update(bound_radius=float("nan")), "bound_radius"),
+    (lambda s: s.update(normal_mode="bogus"), None),
+    (lambda s: s["camera"].update(width=0), "empty"),
+    (lambda s: s["camera"].update(spp=65), "spp"),
+    (lambda s: s["camera"].update(fov_y_deg=180.0), "fov"),
+    (lambda s: s["camera"].update(target=s["camera"]["eye"]), "eye equals target"),
+    (lambda s: s["camera"].update(up=(0.0, 0.0, -1.0)), "parallel"),
+    (lambda s: s["light"].update(dir=(0.0, 0.0, 0.0)), "light direction"),
+    (lambda s: s.update(plane={"n": (0.0, 0.0, 0.0), "o": 0.0}), "plane normal"),
+    (lambda s: s.update(c=(float("inf"), 0.0, 0.0, 0.0)), "not finite"),
+    (lambda s: s["camera"].update(width=40000, height=40000, spp=2), "2^31"),
+])
+def test_bad_julia_arguments_refused(F, mutate, needle):
+    s = W.julia_256(16, 16)
+    mutate(s)
+    if s["normal_mode"] == "bogus":
+        p, pl, cam, li = _structs(dict(s, normal_mode="tetra"))
+        p.normal_mode = 7
+        st = F.fr_render_julia(p, pl, cam, li, F.fr_image(), None)
+        assert st == F.FR_EINVAL and "normal_mode" in F.fr_last_error()
+        return
+    st, msg = _call(F, s)
+    assert st == F.FR_EINVAL
+    assert needle in msg, msg
+
+
+@pytest.mark.parametrize("mutate, needle", [
+    (lambda s: s.update(n=1), "power"),
+    (lambda s: s.update(n=17), "power"),
+    (lambda s: s.update(bailout=0.0), "bailout"),
+    (lambda s: s.update(max_iter=2000), "max_iter"),
+])
+def test_bad_bulb_arguments_refused(F, mutate, needle):
+    s = W.bulb_1080p(0, 16, 16)
+    mutate(s)
+    st, msg = _call(F, s)
+    assert st == F.FR_EINVAL and needle in msg, msg
+
+
+def test_no_output_refused(F):
+    st, msg = _call(F, W.julia_256(16, 16))
+    assert st == F.FR_EINVAL and "no output" in msg
+
+
+def test_null_structs_refused(F):
+    p, pl, cam, li = _structs(W.julia_256(16, 16))
+    lib = F.load()
+    img = F.fr_image()
+    assert lib.fr_render_julia(None, None, ctypes.byref(cam), ctypes.byref(li), ctypes.byref(img), None) == F.FR_EINVAL
+    assert lib.fr_render_julia(ctypes.byref(p), None, None, ctypes.byref(li), ctypes.byref(img), None) == F.FR_EINVAL
+    assert lib.fr_render_julia(ctypes.byref(p), None, ctypes.byref(cam), None, ctypes.byref(img), None) == F.FR_EINVAL
+    assert lib.fr_render_julia(ctypes.byref(p), None, ctypes.byref(cam), ctypes.byref(li), None, None) == F.FR_EINVAL
+
+
+def test_tuning_roundtrip_and_checks(F):
+    t = F.fr_get_tuning()
+    old = (t.plain_block, t.plain_unroll, t.persist_block, t.persist_ctas_per_sm,
+           t.refill_threshold, t.persist_unroll)
+    bad = F.fr_tuning(*old)
+    bad.plain_block = 48
+    assert F.fr_set_tuning(bad) == F.FR_EINVAL
+    bad = F.fr_tuning(*old)
+    bad.persist_unroll = 3
+    assert F.fr_set_tuning(bad) == F.FR_EINVAL
+    bad = F.fr_tuning(*old)
+    bad.refill_threshold = 0
+    assert F.fr_set_tuning(bad) == F.FR_EINVAL
+    good = F.fr_tuning(*old)
+    good.plain_block = 64
+    assert F.fr_set_tuning(good) == F.FR_OK
+    assert F.fr_get_tuning().plain_block == 64
+    assert F.fr_set_tuning(F.fr_tuning(*old)) == F.FR_OK
