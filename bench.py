@@ -6,7 +6,7 @@ and the cut plane z = 0.1 (camera frame 10 of the orbit), rendered through the
 C ABI.  One step = one full frame (every pixel: camera ray, interval, march,
 normal, shadow ray, shading, stores).  Prints one JSON line.
 
-  python bench.py [--steps K] [--warmup W] [--workload NAME] [--path plain|persistent]
+  python bench.py [--steps K] [--warmup W] [--workload NAME] [--path persistent|plain]
   python -m torch.distributed.run --nproc-per-node N bench.py --gpus N   (weak scaling:
         every rank renders its own frame of the orbit; no data-path collective)
   python bench.py --impl reference    (the CPU oracle on the host cores, same metric)
@@ -20,7 +20,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -28,36 +27,46 @@ sys.path.insert(0, ROOT)
 
 from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 
-# FP32 operations per unit of work, used for the roofline's achieved FLOP/s
-# (units counted per frame by the counting kernel).  Julia degree 2: the orbit
-# step of julia_de2 written out (2 FMUL for |z'|^2, 1 FADD for 2x, 3 FFMA for
-# the imaginary parts, 1 FMUL + 2 FFMA + 2 FADD for the real part, 1 FMUL +
-# 3 FFMA for |z|^2; FFMA = 2) = 24 flops per orbit iteration.  Mandelbulb:
-# FP32 operations the float math library executes for one trip of bulb_de
-# (sqrt, pow, acos, atan2, two sincos, pow) plus the arithmetic around them;
-# provisional estimate until ncu's SASS counters (2*FFMA + FADD + FMUL) are
-# divided by the counted orbit iterations.
-FLOPS_PER_ITER = {("julia", 2): 24.0, ("julia", 3): 31.0, ("bulb", 8): 178.0}
+# FP32 operations per orbit iteration, the unit of work of the roofline's
+# achieved FLOP/s (units counted per step by the counting kernel).  Each figure
+# is the FP32 work the one-ray-per-thread kernel executes per orbit iteration,
+# everything included (orbit step, DE epilogue, march update, stencils, camera
+# ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
+# divided by the iterations counted on the same scene (Mandelbulb n = 8 at
+# 480x270: 803.2 M / 3.187 M = 252; Julia p = 2 at 256x256: 364.9 M / 10.27 M
+# = 35.5).  The degree-3 Julia figure is the degree-2 one scaled by the ratio
+# of their orbit-step arithmetic (28 / 24).
+FLOPS_PER_ITER = {("julia", 2): 35.5, ("julia", 3): 41.4, ("bulb", 8): 252.0}
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32)
 
 
 def workload(name: str, rank: int = 0):
+    """(list of scenes rendered per step, description).  Under torchrun every rank
+    renders its own frame of the orbit (weak scaling)."""
     if name == "bulb_1080p":
-        return W.bulb_1080p(10 + rank), "Mandelbulb n=8 1920x1080, 12 iterations, bailout 2, shadow ray, cut z=0.1, frame %d" % (10 + rank)
+        return [W.bulb_1080p(10 + rank)], ("Mandelbulb n=8 1920x1080, 12 iterations, bailout 2, "
+                                           "shadow ray, cut z=0.1, frame %d" % (10 + rank))
     if name == "bulb_small":
-        return W.bulb_1080p(10 + rank, 480, 270), "Mandelbulb n=8 480x270 (same scene, small case)"
+        return [W.bulb_1080p(10 + rank, 480, 270)], "Mandelbulb n=8 480x270 (same scene, small case)"
     if name == "julia_256":
-        return W.julia_256(), "quaternion Julia q^2+c, c=(-0.2,0.6,0.2,0), 256x256, 11 iterations"
+        return [W.julia_256()], "quaternion Julia q^2+c, c=(-0.2,0.6,0.2,0), 256x256, 11 iterations"
+    if name == "batch_mixed":
+        sc = W.batch_mixed(W.BASE_SEED + rank)
+        return sc, "64 mixed requests (Julia / Mandelbulb), sides 128..2048 log-uniform, %d pixels" % (
+            W.total_pixels(sc))
+    if name == "batch_small":
+        sc = W.batch_mixed(W.BASE_SEED + rank, 64, 5.0, 8.0)
+        return sc, "64 mixed requests, sides 32..256 (small case)"
     if name == "stress_bulb_4k":
-        return W.stress_bulb_4k(60 + rank), "Mandelbulb n=8 3840x2160 4 spp, iteration cap 12 (frame 60)"
+        return [W.stress_bulb_4k(60 + rank)], "Mandelbulb n=8 3840x2160 4 spp, iteration cap 12 (frame 60)"
     if name == "stress_julia_4k":
-        return W.stress_julia_4k(), "quaternion Julia 3840x2160 with shadow rays"
+        return [W.stress_julia_4k()], "quaternion Julia 3840x2160 with shadow rays"
     raise SystemExit("unknown workload " + name)
 
 
 def flops_per_iter(scene) -> float:
     key = (scene["kind"], scene["p"] if scene["kind"] == "julia" else scene["n"])
-    return FLOPS_PER_ITER.get(key, FLOPS_PER_ITER[("bulb", 8)] if scene["kind"] == "bulb" else 24.0)
+    return FLOPS_PER_ITER.get(key, FLOPS_PER_ITER[("bulb", 8)] if scene["kind"] == "bulb" else 35.5)
 
 
 class ClockSampler:
@@ -99,7 +108,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
@@ -108,30 +117,42 @@ def fp32_peak_tflops(clock_mhz: float, sms: int) -> float:
     return sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
 
 
-def run_reference(args, scene, desc, rank, world):
-    """CPU oracle (float build) on the host cores, same metric and units."""
+def _oracle_sample(scenes, stride):
+    """Pixel sample of the step's scenes: every stride-th pixel of each."""
+    import numpy as np
+
+    return [np.arange(0, s["camera"]["width"] * s["camera"]["height"], stride, dtype=np.int64)
+            for s in scenes]
+
+
+def _oracle_rays(oracle, scenes, samples, threads):
+    rays = 0
+    for s, px in zip(scenes, samples):
+        r = oracle.render(s, pixels=px, precision="f32", threads=threads)
+        rays += len(px) * s["camera"]["spp"] + int(r["stats"][:, 4].sum())
+    return rays
+
+
+def run_reference(args, scenes, desc, rank, world):
+    """The CPU oracle (float build) on the host cores: same metric and units,
+    each step a bounded pixel sample of the same workload."""
     if rank != 0:
         return
     import oracle
 
     oracle.build()
     threads = os.cpu_count() or 1
-    n = scene["camera"]["width"] * scene["camera"]["height"]
-    # a bounded sample: every k-th pixel row-interleaved, sized to a few seconds per step
-    stride = max(1, n // 400_000)
-    import numpy as np
-
-    px = np.arange(0, n, stride, dtype=np.int64)
-    for _ in range(args.warmup):
-        oracle.render(scene, pixels=px[: min(len(px), 20000)], precision="f32", threads=threads)
+    n = sum(s["camera"]["width"] * s["camera"]["height"] for s in scenes)
+    stride = max(1, n // 2_000_000)
+    samples = _oracle_sample(scenes, stride)
+    _oracle_rays(oracle, scenes, _oracle_sample(scenes, stride * 16), threads)  # warm-up
     t0 = time.perf_counter()
     rays = 0
     for _ in range(args.steps):
-        r = oracle.render(scene, pixels=px, precision="f32", threads=threads)
-        rays += len(px) * scene["camera"]["spp"] + int(r["stats"][:, 4].sum())
+        rays += _oracle_rays(oracle, scenes, samples, threads)
     dt = time.perf_counter() - t0
     value = rays / dt / 1e6
-    sample = "every %d-th pixel of the frame (%d pixels per step)" % (stride, len(px))
+    sample = "every %d-th pixel of each image (%d pixels per step)" % (stride, sum(map(len, samples)))
     print(json.dumps({
         "impl": "reference", "metric": "Mrays/s", "value": value, "unit": "Mrays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -144,30 +165,106 @@ def run_reference(args, scene, desc, rank, world):
     }))
 
 
-def cpu_baseline(scene, budget_s: float = 12.0):
-    """The float oracle on all host cores over a bounded pixel sample."""
-    import numpy as np
-
+def cpu_baseline(scenes, budget_s: float = 12.0):
+    """The float oracle on all host cores over a bounded pixel sample of the
+    same workload, grown until it takes about budget_s."""
     import oracle
 
     oracle.build()
     threads = os.cpu_count() or 1
-    n = scene["camera"]["width"] * scene["camera"]["height"]
-    stride = 64
-    t0 = time.perf_counter()
-    px = np.arange(0, n, stride, dtype=np.int64)
-    r = oracle.render(scene, pixels=px, precision="f32", threads=threads)
-    dt = time.perf_counter() - t0
-    # grow the sample to the time budget (bounded)
-    if dt < budget_s / 4 and stride > 1:
-        stride = max(1, int(stride * dt / (budget_s / 2)))
-        px = np.arange(0, n, stride, dtype=np.int64)
+    stride = 256
+    while True:
+        samples = _oracle_sample(scenes, stride)
         t0 = time.perf_counter()
-        r = oracle.render(scene, pixels=px, precision="f32", threads=threads)
+        rays = _oracle_rays(oracle, scenes, samples, threads)
         dt = time.perf_counter() - t0
-    rays = len(px) * scene["camera"]["spp"] + int(r["stats"][:, 4].sum())
+        if dt >= budget_s / 3 or stride == 1:
+            break
+        stride = max(1, int(stride * dt / budget_s) if dt > 0 else 1)
+    reps = 1
+    while dt * (reps + 1) / reps < budget_s and reps < 20 and dt < budget_s:
+        t1 = time.perf_counter()
+        rays += _oracle_rays(oracle, scenes, samples, threads)
+        dt += time.perf_counter() - t1
+        reps += 1
     return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": "every %d-th pixel of the same frame (%d pixels, %.1f s)" % (stride, len(px), dt)}
+            "sample": "every %d-th pixel of each image, %d pass(es), %.1f s" % (stride, reps, dt)}
+
+
+class Renderer:
+    """Prebuilt C structs for a list of scenes and their outputs, so that a timed
+    step is only the C calls (no Python marshalling of parameters)."""
+
+    def __init__(self, api, F, scenes, outs, path, stream, ws=None):
+        self.F, self.path, self.stream = F, path, stream
+        self.n = len(scenes)
+        if path == "plain":
+            self.calls = []
+            for s, o in zip(scenes, outs):
+                fn = F.fr_render_julia if s["kind"] == "julia" else F.fr_render_mandelbulb
+                prm = api.julia_params(s) if s["kind"] == "julia" else api.bulb_params(s)
+                self.calls.append((fn, prm, api.plane_struct(s), api.camera_struct(s),
+                                   api.light_struct(s), api.image_struct(o)))
+        else:
+            self.arr = api.request_array(scenes, outs)
+            self.ws = ws if ws is not None else api.workspace(self.n)
+
+    def launches(self) -> int:
+        return self.n if self.path == "plain" else (self.n + 63) // 64
+
+    def __call__(self):
+        if self.path == "plain":
+            for fn, prm, pl, cam, li, img in self.calls:
+                self.F.check(fn(prm, pl, cam, li, img, self.stream))
+        else:
+            self.F.check(self.F.fr_render_batch(self.arr, self.n, self.ws.data_ptr(), self.ws.numel(),
+                                                self.stream))
+
+
+def time_steps(torch, step, steps, stream, flush, dist=None, clk_index=None):
+    """K steps, each bracketed by CUDA events on the launching stream, with the
+    L2 flushed (256 MB write) between steps outside the events.  Returns the
+    per-step device times (ms), the max over ranks of their sum (s) and clocks."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(clk_index) if clk_index is not None else None
+    if clk:
+        clk.__enter__()
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    if dist:
+        dist.barrier()
+    times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total = sum(times) / 1e3
+    if dist:
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return times, total, (clk.summary() if clk else None)
+
+
+def count_frame(api, torch, scenes):
+    """Counting-kernel pass (untimed): summed FR_STAT_* counters of all scenes."""
+    tot = [0] * 6
+    for s in scenes:
+        c = api.render(s, rgba8=False, depth=False, stats=True)
+        torch.cuda.synchronize()
+        for k, v in enumerate(c["stats"].cpu().tolist()):
+            tot[k] += int(v)
+    return tot
+
+
+def flops_of(scenes, per_scene_iters):
+    return sum(flops_per_iter(s) * it for s, it in zip(scenes, per_scene_iters))
 
 
 def main():
@@ -177,18 +274,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bulb_1080p")
-    ap.add_argument("--path", default="plain", choices=["plain"])
+    ap.add_argument("--path", default="persistent", choices=["plain", "persistent"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
-    scene, desc = workload(args.workload, rank)
+    scenes, desc = workload(args.workload, rank)
 
     if args.impl == "reference":
-        run_reference(args, scene, desc, rank, world)
+        run_reference(args, scenes, desc, rank, world)
         return
 
     import torch
@@ -201,109 +299,117 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
+    from paper_2102_01747_gb300 import _ffi as F
     from paper_2102_01747_gb300 import api, build as B
 
     B.build()
-    from paper_2102_01747_gb300 import _ffi
+    F.load()
+    stream = api.current_stream(dev)
+    tstream = torch.cuda.current_stream(dev)
 
-    _ffi.load()
-    stream = torch.cuda.current_stream(dev)
-    H, Wd = scene["camera"]["height"], scene["camera"]["width"]
-    spp = scene["camera"]["spp"]
+    counts = count_frame(api, torch, scenes)
+    per_scene_iters = []
+    if len(scenes) > 1:
+        for s in scenes:
+            per_scene_iters.append(count_frame(api, torch, [s])[5])
+    else:
+        per_scene_iters = [counts[5]]
+    rays_per_step = counts[0] + counts[1]
+    de_per_step = counts[2] + counts[3] + counts[4]
+    iters_per_step = counts[5]
+    flops_per_step = flops_of(scenes, per_scene_iters)
 
-    # counting pass (untimed): rays, DE calls and orbit iterations of one frame
-    cnt = api.render(scene, rgba8=False, depth=False, stats=True)
-    torch.cuda.synchronize()
-    stats = [int(v) for v in cnt["stats"].cpu().tolist()]
-    rays_per_frame = stats[0] + stats[1]
-    de_per_frame = stats[2] + stats[3] + stats[4]
-    iters_per_frame = stats[5]
-
-    out = api.alloc_image(scene, rgba8=True, depth=True)
+    outs = [api.alloc_image(s, rgba8=True, depth=True) for s in scenes]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def step():
-        api.render(scene, out=out)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()  # L2 flushed between timed frames (outside the events)
-            starts[i].record(stream)
+    paths = [args.path] + ([] if args.no_compare else [p for p in ("plain", "persistent") if p != args.path])
+    results = {}
+    for path in paths:
+        step = Renderer(api, F, scenes, outs, path, stream)
+        for _ in range(args.warmup):
             step()
-            ends[i].record(stream)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    times_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(times_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    kernel_ms = statistics.mean(times_ms)
-    rays_total = rays_per_frame * args.steps * world
-    value = rays_total / total_s / 1e6
+        times, total_s, clk = time_steps(torch, step, args.steps, tstream, flush, dist,
+                                         clk_index=local if path == args.path else None)
+        results[path] = {"times": times, "total_s": total_s, "clk": clk, "launches": step.launches()}
 
-    # end to end through the public API with host buffers: the scene parameters
-    # go in with the call, the image (rgba8 + depth) comes back to pinned memory
-    host_rgba = torch.empty((H, Wd), dtype=torch.int32, pin_memory=True)
-    host_depth = torch.empty((H, Wd), dtype=torch.float32, pin_memory=True)
+    main_r = results[args.path]
+    total_s = main_r["total_s"]
+    value = rays_per_step * args.steps * world / total_s / 1e6
+    kernel_ms = statistics.mean(main_r["times"]) / main_r["launches"]
+
+    # end to end through the public API with host buffers: the scene parameters go
+    # in with the call, every image (rgba8 + depth) comes back to pinned memory
+    hosts = [(torch.empty(o["rgba8"].shape, dtype=torch.int32, pin_memory=True),
+              torch.empty(o["depth"].shape, dtype=torch.float32, pin_memory=True)) for o in outs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o = api.render(scene, out=out)
-        host_rgba.copy_(o["rgba8"], non_blocking=True)
-        host_depth.copy_(o["depth"], non_blocking=True)
+        if args.path == "plain":
+            for s, o in zip(scenes, outs):
+                api.render(s, out=o)
+        else:
+            api.render_batch(scenes, outs)
+        for (hr, hd), o in zip(hosts, outs):
+            hr.copy_(o["rgba8"], non_blocking=True)
+            hd.copy_(o["depth"], non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = rays_per_frame * args.steps / e2e_s / 1e6
+    e2e_value = rays_per_step * args.steps / e2e_s / 1e6
+    in_bytes = ctypes_sizeof_inputs(F, len(scenes))
+    out_bytes = sum(o["rgba8"].numel() * 4 + o["depth"].numel() * 4 for o in outs)
 
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    c = clk.summary()
+    c = main_r["clk"] or {}
     max_mhz = c.get("sm_max_mhz") or 2070.0
     peak = fp32_peak_tflops(max_mhz, sms)
-    fpi = flops_per_iter(scene)
-    achieved = fpi * iters_per_frame / (kernel_ms / 1e3) / 1e12
+    achieved = flops_per_step / main_r["launches"] / (kernel_ms / 1e3) / 1e12
 
     if rank != 0:
         return
+    kern = "plain_kernel" if args.path == "plain" else "persist_kernel"
     res = {
         "metric": "Mrays/s", "value": value, "unit": "Mrays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "path": args.path, "width": Wd, "height": H, "spp": spp,
-                   "l2": "flushed between timed frames (256 MB write)",
+        "config": {"workload": desc, "path": args.path, "requests": len(scenes),
+                   "pixels_per_step": sum(s["camera"]["width"] * s["camera"]["height"] for s in scenes),
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas (one frame per rank)" if world > 1 else "single GPU"},
-        "de_evals_per_s": de_per_frame * args.steps * world / total_s,
-        "orbit_iters_per_s": iters_per_frame * args.steps * world / total_s,
-        "per_frame": {"rays": rays_per_frame, "primary_rays": stats[0], "shadow_rays": stats[1],
-                      "de_calls": de_per_frame, "orbit_iters": iters_per_frame},
+        "de_evals_per_s": de_per_step * args.steps * world / total_s,
+        "orbit_iters_per_s": iters_per_step * args.steps * world / total_s,
+        "per_step": {"rays": rays_per_step, "primary_rays": counts[0], "shadow_rays": counts[1],
+                     "de_calls": de_per_step, "orbit_iters": iters_per_step},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "plain_kernel<%s>" % scene["kind"],
-                     "flops_per_orbit_iter": fpi,
-                     "peak_basis": "FP32 FFMA: %d SMs x %d lanes x 2 x %.0f MHz" % (sms, FP32_LANES_PER_SM, max_mhz),
-                     "frac_at_observed_clock": (achieved / fp32_peak_tflops(c["sm_mhz"], sms)) if c.get("sm_mhz") else None},
-        "e2e": {"value": e2e_value, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": H * Wd * 8,
-                "note": "inputs are scene parameters passed by value in the call (kernel parameters)"},
-        "gpu_launches": args.steps,
+                     "frac": achieved / peak, "traffic": None, "kernel": kern,
+                     "flops_per_step": flops_per_step,
+                     "peak_basis": "FP32 FFMA: %d SMs x %d lanes x 2 flops x %.0f MHz (max clock)" % (
+                         sms, FP32_LANES_PER_SM, max_mhz),
+                     "frac_at_observed_clock": (achieved / fp32_peak_tflops(c["sm_mhz"], sms))
+                     if c.get("sm_mhz") else None},
+        "e2e": {"value": e2e_value, "unit": "Mrays/s", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": out_bytes,
+                "note": "inputs are the scene parameter structs passed in each call"},
+        "gpu_launches": main_r["launches"] * args.steps,
         "clocks": c,
     }
+    for path, r in results.items():
+        if path != args.path:
+            res["other_path"] = {"path": path,
+                                 "value": rays_per_step * args.steps * world / r["total_s"] / 1e6,
+                                 "ms_per_step": r["total_s"] / args.steps * 1e3}
+            res["speedup_vs_" + path] = r["total_s"] / total_s
     if world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(scene)
+        res["cpu_baseline"] = cpu_baseline(scenes)
     print(json.dumps(res))
+
+
+def ctypes_sizeof_inputs(F, n):
+    import ctypes
+
+    return n * (ctypes.sizeof(F.fr_request) - ctypes.sizeof(F.fr_image))
 
 
 if __name__ == "__main__":

@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "../../include/fr.h"
 #include "fr_launch.h"
@@ -261,17 +263,62 @@ FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_pla
                                      (cudaStream_t)stream));
 }
 
+// one 256-byte slot (queue head) per launch of up to kMaxReqPerLaunch requests
 FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs)
 {
-    (void)n_reqs;
-    return 0;
+    if (n_reqs < 1) return 0;
+    return (size_t)256 * (size_t)((n_reqs + fr::kMaxReqPerLaunch - 1) / fr::kMaxReqPerLaunch);
 }
 
 FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *workspace,
                                  size_t ws_bytes, void *stream)
 {
-    (void)reqs; (void)n_reqs; (void)workspace; (void)ws_bytes; (void)stream;
-    return fail(FR_ENOTIMPL, "fr_render_batch not built yet");
+    if (!reqs) return fail(FR_EINVAL, "requests is NULL");
+    if (n_reqs < 1 || n_reqs > 4096) return fail(FR_EINVAL, "n_reqs %d outside 1..4096", n_reqs);
+    if (!workspace) return fail(FR_EINVAL, "workspace is NULL");
+    if (!aligned(workspace, 256)) return fail(FR_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < fr_batch_workspace_bytes(n_reqs))
+        return fail(FR_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, fr_batch_workspace_bytes(n_reqs));
+    // check every request before launching anything
+    static thread_local fr::BatchArgs A;
+    std::vector<fr::DevReq> all((size_t)n_reqs);
+    bool count = false;
+    for (int i = 0; i < n_reqs; i++) {
+        fr::DevReq &R = all[(size_t)i];
+        std::memset(&R, 0, sizeof R);
+        const fr_request &q = reqs[i];
+        fr_status st;
+        if (q.kind == FR_KIND_JULIA)
+            st = resolve_julia(R, &q.julia);
+        else if (q.kind == FR_KIND_BULB)
+            st = resolve_bulb(R, &q.bulb);
+        else
+            st = fail(FR_EINVAL, "kind %d unknown", q.kind);
+        if (st == FR_OK) st = resolve_common(R, &q.plane, &q.camera, &q.light, &q.out);
+        if (st != FR_OK) {
+            g_err = "request " + std::to_string(i) + ": " + g_err;
+            return st;
+        }
+        count = count || q.out.stats != nullptr;
+    }
+    const fr_tuning tu = tuning();
+    for (int first = 0, chunk = 0; first < n_reqs; first += fr::kMaxReqPerLaunch, chunk++) {
+        const int n = std::min(fr::kMaxReqPerLaunch, n_reqs - first);
+        long long units = 0;
+        for (int i = 0; i < n; i++) {
+            A.reqs[i] = all[(size_t)(first + i)];
+            A.reqs[i].unit_begin = units;
+            units += A.reqs[i].n_units;
+        }
+        A.n_reqs = n;
+        A.total_units = units;
+        A.refill_threshold = tu.refill_threshold;
+        A.queue = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 256 * (size_t)chunk);
+        const fr_status st = launched(fr::launch_persist(A, tu.persist_block, tu.persist_ctas_per_sm,
+                                                         tu.persist_unroll, count, (cudaStream_t)stream));
+        if (st != FR_OK) return st;
+    }
+    return FR_OK;
 }
 
 FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,

@@ -162,100 +162,149 @@ __device__ __forceinline__ bool bounds(const DevReq &R, float3 ro, float3 rd, fl
 }
 
 // ------------------------------------------------------------------ distance estimators
-// Quaternion Julia DE, degree 2: |z'|^2 *= 4 |z|^2 before each z <- z^2 + c,
-// z^2 = (x^2 - |v|^2, 2 x v) for z = (x, v); stop once |z|^2 > esc2;
-// d = 0.25 log|z|^2 sqrt(|z|^2 / |z'|^2).
+// Each DE is written as init / one orbit step / distance so that the one-ray-
+// per-thread kernel (whole orbit in a loop) and the persistent kernel (orbit
+// steps interleaved with other lanes' work) run exactly the same arithmetic.
+//
+// Quaternion Julia (Listing "Julia Set distance", Eqs. 2-4): z0 = (p, slice_w),
+// |z'|^2 = 1; each step multiplies |z'|^2 by p^2 |z|^(2(p-1)) and then sets
+// z <- z^p + c; the orbit stops once |z|^2 > esc2 or after max_iter steps;
+// d = 0.25 log|z|^2 sqrt(|z|^2 / |z'|^2) (= 0.5 |z| log|z| / |z'|).
+struct Orbit {
+    float a, b, c, d;  // Julia: z = (a, b, c, d)      Mandelbulb: w = (a, b, c)
+    float dz;          // Julia: |z'|^2                Mandelbulb: |w'|
+    float m;           // |z|^2 (|w|^2) of the current iterate
+};
+
+__device__ __forceinline__ void julia_init(Orbit &o, float3 p, float slice_w)
+{
+    o.a = p.x; o.b = p.y; o.c = p.z; o.d = slice_w;
+    o.m = o.a * o.a + o.b * o.b + o.c * o.c + o.d * o.d;
+    o.dz = 1.0f;
+}
+
+// degree 2: z^2 = (x^2 - |v|^2, 2 x v) for z = (x, v); |z'|^2 *= 4 |z|^2
+__device__ __forceinline__ void julia2_step(Orbit &o, const float4 c)
+{
+    o.dz *= 4.0f * o.m;
+    const float tx = o.a + o.a;
+    const float nx = o.a * o.a - (o.b * o.b + o.c * o.c + o.d * o.d) + c.x;
+    o.b = tx * o.b + c.y;
+    o.c = tx * o.c + c.z;
+    o.d = tx * o.d + c.w;
+    o.a = nx;
+    o.m = o.a * o.a + o.b * o.b + o.c * o.c + o.d * o.d;
+}
+
+// degree 3 (the listing's cube): z^3 = (x^3 - 3x|v|^2, (3x^2 - |v|^2) v); |z'|^2 *= 9 |z|^4
+__device__ __forceinline__ void julia3_step(Orbit &o, const float4 c)
+{
+    o.dz *= 9.0f * (o.m * o.m);
+    const float x2 = o.a * o.a;
+    const float v2 = o.b * o.b + o.c * o.c + o.d * o.d;
+    const float f = 3.0f * x2 - v2;
+    const float nx = o.a * (x2 - 3.0f * v2) + c.x;
+    o.b = f * o.b + c.y;
+    o.c = f * o.c + c.z;
+    o.d = f * o.d + c.w;
+    o.a = nx;
+    o.m = o.a * o.a + o.b * o.b + o.c * o.c + o.d * o.d;
+}
+
+__device__ __forceinline__ float julia_dist(const Orbit &o)
+{
+    return 0.25f * logf(o.m) * sqrtf(o.m / o.dz);
+}
+
+// Mandelbulb (Listing "Mandelbulb distance", Eq. 1): w0 = c, dz = 1; each step
+// dz <- n r^(n-1) dz + 1 and w <- r^n (sin b sin a, cos b, sin b cos a) + c with
+// r = |w|, b = n acos(w.y / r) (y/r clamped to [-1, 1]), a = n atan2(w.x, w.z);
+// r = 0 gives the zero power.  d = 0.25 log(m) sqrt(m) / dz.
+__device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
+{
+    o.a = p.x; o.b = p.y; o.c = p.z; o.d = 0.0f;
+    o.m = o.a * o.a + o.b * o.b + o.c * o.c;
+    o.dz = 1.0f;
+}
+
+__device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
+{
+    const float nf = (float)n;
+    const float r = sqrtf(o.m);
+    o.dz = nf * powf(r, nf - 1.0f) * o.dz + 1.0f;
+    float px = 0.0f, py = 0.0f, pz = 0.0f;
+    if (r > 0.0f) {
+        const float ct = fminf(fmaxf(o.b / r, -1.0f), 1.0f);
+        const float b = nf * acosf(ct);
+        const float a = nf * atan2f(o.a, o.c);
+        float sb, cb, sa, ca;
+        sincosf(b, &sb, &cb);
+        sincosf(a, &sa, &ca);
+        const float rn = powf(r, nf);
+        px = rn * (sb * sa);
+        py = rn * cb;
+        pz = rn * (sb * ca);
+    }
+    o.a = px + cpt.x;
+    o.b = py + cpt.y;
+    o.c = pz + cpt.z;
+    o.m = o.a * o.a + o.b * o.b + o.c * o.c;
+}
+
+__device__ __forceinline__ float bulb_dist(const Orbit &o)
+{
+    return 0.25f * logf(o.m) * sqrtf(o.m) / o.dz;
+}
+
+// whole-orbit DEs (one-ray-per-thread kernel); trips = orbit loop trips
 template <int U>
 __device__ __forceinline__ float julia_de2(const float4 c, float slice_w, int max_iter, float esc2,
                                            float3 p, int &trips)
 {
-    float x = p.x, y = p.y, z = p.z, w = slice_w;
-    float m2 = x * x + y * y + z * z + w * w;
-    float dz2 = 1.0f;
+    Orbit o;
+    julia_init(o, p, slice_w);
     int i = 0;
 #pragma unroll U
     for (int k = 0; k < max_iter; k++) {
-        dz2 *= 4.0f * m2;
-        float tx = x + x;
-        float nx = x * x - (y * y + z * z + w * w) + c.x;
-        y = tx * y + c.y;
-        z = tx * z + c.z;
-        w = tx * w + c.w;
-        x = nx;
-        m2 = x * x + y * y + z * z + w * w;
+        julia2_step(o, c);
         i++;
-        if (m2 > esc2) break;
+        if (o.m > esc2) break;
     }
     trips = i;
-    return 0.25f * logf(m2) * sqrtf(m2 / dz2);
+    return julia_dist(o);
 }
 
-// degree 3 (the listing's cube): |z'|^2 *= 9 |z|^4, z^3 = (x^3 - 3x|v|^2, (3x^2 - |v|^2) v)
 template <int U>
 __device__ __forceinline__ float julia_de3(const float4 c, float slice_w, int max_iter, float esc2,
                                            float3 p, int &trips)
 {
-    float x = p.x, y = p.y, z = p.z, w = slice_w;
-    float m2 = x * x + y * y + z * z + w * w;
-    float dz2 = 1.0f;
+    Orbit o;
+    julia_init(o, p, slice_w);
     int i = 0;
 #pragma unroll U
     for (int k = 0; k < max_iter; k++) {
-        dz2 *= 9.0f * (m2 * m2);
-        float x2 = x * x;
-        float v2 = y * y + z * z + w * w;
-        float f = 3.0f * x2 - v2;
-        float nx = x * (x2 - 3.0f * v2) + c.x;
-        y = f * y + c.y;
-        z = f * z + c.z;
-        w = f * w + c.w;
-        x = nx;
-        m2 = x * x + y * y + z * z + w * w;
+        julia3_step(o, c);
         i++;
-        if (m2 > esc2) break;
+        if (o.m > esc2) break;
     }
     trips = i;
-    return 0.25f * logf(m2) * sqrtf(m2 / dz2);
+    return julia_dist(o);
 }
 
-// Mandelbulb DE: w0 = c, m = |w|^2, dz = 1; per trip dz <- n r^(n-1) dz + 1 and
-// w <- r^n (sin b sin a, cos b, sin b cos a) + c with b = n acos(w.y / r) (y/r
-// clamped to [-1, 1]), a = n atan2(w.x, w.z); stop once m > bailout^2;
-// d = 0.25 log(m) sqrt(m) / dz.  r = 0 gives the zero power.
 template <int U>
 __device__ __forceinline__ float bulb_de(int n, int max_iter, float esc2, float3 c, int &trips)
 {
-    float wx = c.x, wy = c.y, wz = c.z;
-    float m = wx * wx + wy * wy + wz * wz;
-    float dz = 1.0f;
-    const float nf = (float)n;
+    Orbit o;
+    bulb_init(o, c);
     int i = 0;
 #pragma unroll U
     for (int k = 0; k < max_iter; k++) {
-        float r = sqrtf(m);
-        dz = nf * powf(r, nf - 1.0f) * dz + 1.0f;
-        float px = 0.0f, py = 0.0f, pz = 0.0f;
-        if (r > 0.0f) {
-            float ct = fminf(fmaxf(wy / r, -1.0f), 1.0f);
-            float b = nf * acosf(ct);
-            float a = nf * atan2f(wx, wz);
-            float sb, cb, sa, ca;
-            sincosf(b, &sb, &cb);
-            sincosf(a, &sa, &ca);
-            float rn = powf(r, nf);
-            px = rn * (sb * sa);
-            py = rn * cb;
-            pz = rn * (sb * ca);
-        }
-        wx = px + c.x;
-        wy = py + c.y;
-        wz = pz + c.z;
-        m = wx * wx + wy * wy + wz * wz;
+        bulb_step(o, c, n);
         i++;
-        if (m > esc2) break;
+        if (o.m > esc2) break;
     }
     trips = i;
-    return 0.25f * logf(m) * sqrtf(m) / dz;
+    return bulb_dist(o);
 }
 
 template <int KIND, int U>
@@ -266,6 +315,52 @@ __device__ __forceinline__ float de(const DevReq &R, float3 p, int &trips)
         return julia_de3<U>(R.c, R.slice_w, R.max_iter, R.esc2, p, trips);
     }
     return bulb_de<U>(R.power, R.max_iter, R.esc2, p, trips);
+}
+
+// ------------------------------------------------------------------ normal stencils
+// Tap k of the stencil around x and its contribution to the gradient sum g.
+// Tetrahedral (Eq. 5, Listing "Normal calculation"): taps x + h nu_k with
+// nu = (1,-1,-1), (-1,-1,1), (-1,1,-1), (1,1,1), g += (h nu_k) d_k.
+// Central: taps x +- h e_j in the order +x, -x, +y, -y, +z, -z,
+// g_j = d(x + h e_j) - d(x - h e_j).
+__device__ __forceinline__ float3 tap_point(float3 x, int mode, float h, int k)
+{
+    if (mode == 0) {
+        const float sx = (k == 0 || k == 3) ? h : -h;
+        const float sy = (k >= 2) ? h : -h;
+        const float sz = (k == 1 || k == 3) ? h : -h;
+        return v3(x.x + sx, x.y + sy, x.z + sz);
+    }
+    const float s = (k & 1) ? -h : h;
+    return v3(x.x + (k < 2 ? s : 0.0f), x.y + ((k >> 1) == 1 ? s : 0.0f), x.z + (k >= 4 ? s : 0.0f));
+}
+
+__device__ __forceinline__ void tap_accum(float3 &g, int mode, float h, int k, float d)
+{
+    if (mode == 0) {
+        const float sx = (k == 0 || k == 3) ? h : -h;
+        const float sy = (k >= 2) ? h : -h;
+        const float sz = (k == 1 || k == 3) ? h : -h;
+        g.x = fmaf(sx, d, g.x);
+        g.y = fmaf(sy, d, g.y);
+        g.z = fmaf(sz, d, g.z);
+        return;
+    }
+    const int j = k >> 1;
+    if (j == 0)
+        g.x = (k & 1) ? g.x - d : d;
+    else if (j == 1)
+        g.y = (k & 1) ? g.y - d : d;
+    else
+        g.z = (k & 1) ? g.z - d : d;
+}
+
+// unit gradient, -rd when it is zero or not finite
+__device__ __forceinline__ float3 finish_normal(float3 g, float3 rd)
+{
+    const float l = sqrtf(dot3(g, g));
+    if (!(l > 0.0f) || !isfinite(l)) return rd * -1.0f;
+    return v3(g.x / l, g.y / l, g.z / l);
 }
 
 // ------------------------------------------------------------------ shading

@@ -35,43 +35,22 @@ __device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, flo
     return hit;
 }
 
-// Normal = normalised gradient of the DE at x.  Tetrahedral stencil (Eq. 5):
-// g = sum_k (h nu_k) d(x + h nu_k) with nu = (1,-1,-1), (-1,-1,1), (-1,1,-1),
-// (1,1,1); central: g_j = d(x + h e_j) - d(x - h e_j).  A zero or non-finite
-// gradient gives -rd.
+// Normal = normalised gradient of the DE at x from the stencil taps of
+// tap_point / tap_accum (tetrahedral Eq. 5 or central differences); a zero or
+// non-finite gradient gives -rd.
 template <int KIND, int U, bool COUNT>
 __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd, Counters &cnt)
 {
-    const float h = R.normal_h;
-    float3 g;
-    int tr0, tr1, tr2, tr3;
-    if (R.normal_mode == 0) {
-        float d0 = de<KIND, U>(R, v3(x.x + h, x.y - h, x.z - h), tr0);
-        float d1 = de<KIND, U>(R, v3(x.x - h, x.y - h, x.z + h), tr1);
-        float d2 = de<KIND, U>(R, v3(x.x - h, x.y + h, x.z - h), tr2);
-        float d3 = de<KIND, U>(R, v3(x.x + h, x.y + h, x.z + h), tr3);
-        g = v3(h * (d0 - d1 - d2 + d3), h * (-d0 - d1 + d2 + d3), h * (-d0 + d1 - d2 + d3));
-        if (COUNT) {
-            cnt.v[kStatNormalDE] += 4;
-            cnt.v[kStatOrbit] += tr0 + tr1 + tr2 + tr3;
-        }
-    } else {
-        int tr4, tr5;
-        float dxp = de<KIND, U>(R, v3(x.x + h, x.y, x.z), tr0);
-        float dxm = de<KIND, U>(R, v3(x.x - h, x.y, x.z), tr1);
-        float dyp = de<KIND, U>(R, v3(x.x, x.y + h, x.z), tr2);
-        float dym = de<KIND, U>(R, v3(x.x, x.y - h, x.z), tr3);
-        float dzp = de<KIND, U>(R, v3(x.x, x.y, x.z + h), tr4);
-        float dzm = de<KIND, U>(R, v3(x.x, x.y, x.z - h), tr5);
-        g = v3(dxp - dxm, dyp - dym, dzp - dzm);
-        if (COUNT) {
-            cnt.v[kStatNormalDE] += 6;
-            cnt.v[kStatOrbit] += tr0 + tr1 + tr2 + tr3 + tr4 + tr5;
-        }
+    const int taps = R.normal_mode == 0 ? 4 : 6;
+    float3 g = v3(0.0f, 0.0f, 0.0f);
+    for (int k = 0; k < taps; k++) {
+        int trips;
+        const float d = de<KIND, U>(R, tap_point(x, R.normal_mode, R.normal_h, k), trips);
+        tap_accum(g, R.normal_mode, R.normal_h, k, d);
+        if (COUNT) cnt.v[kStatOrbit] += trips;
     }
-    float l = sqrtf(dot3(g, g));
-    if (!(l > 0.0f) || !isfinite(l)) return rd * -1.0f;
-    return v3(g.x / l, g.y / l, g.z / l);
+    if (COUNT) cnt.v[kStatNormalDE] += taps;
+    return finish_normal(g, rd);
 }
 
 // One camera sample: interval, march, normal (the plane's for a cut-face hit:

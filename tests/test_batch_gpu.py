@@ -1,0 +1,137 @@
+"""Persistent batched kernel (fr_render_batch) on the GPU: per-request outputs
+equal the one-ray-per-thread kernel's, every request matches the oracle, and
+the batch bookkeeping (several launches, workspace, counters) holds."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2102_01747_gb300 import workloads as W
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 8
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2102_01747_gb300 import api as A
+    from paper_2102_01747_gb300 import build as B
+
+    B.build()
+    return A
+
+
+def _np(outs):
+    import torch
+
+    torch.cuda.synchronize()
+    return [{k: v.cpu().numpy() for k, v in o.items()} for o in outs]
+
+
+def small_mixed(n=10, seed=5):
+    """The mixed-batch recipe (alternating Julia / Mandelbulb, random c, n, iterations,
+    cut planes and cameras) at sides 24..200 so the oracle can check every pixel."""
+    return W.batch_mixed(seed=seed, n_requests=n, min_log2=4.6, max_log2=7.65)
+
+
+def tuned(F, **kw):
+    old = F.fr_get_tuning()
+    t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+    for k, v in kw.items():
+        setattr(t, k, v)
+    assert F.fr_set_tuning(t) == F.FR_OK
+    return F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+
+
+def test_single_request_equals_plain(api):
+    for scene in (W.bulb_1080p(10, 320, 180), W.julia_256(200, 150)):
+        plain = _np([api.render(scene, rgba8=True, depth=True, saved=True)])[0]
+        batch = _np(api.render_batch([scene], rgba8=True, depth=True, saved=True))[0]
+        for k in ("rgba8", "depth", "saved"):
+            assert np.array_equal(plain[k], batch[k]), k
+
+
+def test_mixed_batch_equals_plain_and_oracle(api, orc):
+    scenes = small_mixed()
+    batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    for s, b in zip(scenes, batch):
+        p = _np([api.render(s, rgba8=True, depth=True)])[0]
+        assert np.array_equal(p["rgba8"], b["rgba8"])
+        assert np.array_equal(p["depth"], b["depth"])
+        o = orc.render(s, precision="f32", threads=THREADS)
+        res = compare(b["rgba8"].reshape(-1), b["depth"].reshape(-1), o["rgba8"], o["depth"])
+        assert res["ok"], res
+
+
+def test_more_requests_than_one_launch(api):
+    """70 requests -> two launches, each with its own queue head."""
+    from paper_2102_01747_gb300 import _ffi as F
+
+    scenes = [W.julia_256(8 + (i % 5) * 7, 5 + (i % 3) * 4) if i % 2 else
+              W.bulb_1080p(i, 9 + (i % 4) * 5, 7 + (i % 6) * 3) for i in range(70)]
+    assert F.fr_batch_workspace_bytes(70) == 512
+    batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    for s, b in zip(scenes, batch):
+        p = _np([api.render(s, rgba8=True, depth=True)])[0]
+        assert np.array_equal(p["rgba8"], b["rgba8"])
+
+
+@pytest.mark.parametrize("kw", [
+    dict(refill_threshold=1), dict(refill_threshold=32), dict(persist_unroll=1),
+    dict(persist_unroll=4), dict(persist_block=64, persist_ctas_per_sm=1), dict(persist_block=256)])
+def test_schedule_does_not_change_images(api, kw):
+    from paper_2102_01747_gb300 import _ffi as F
+
+    scenes = small_mixed(6, seed=9)
+    ref = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    old = tuned(F, **kw)
+    try:
+        got = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    finally:
+        F.fr_set_tuning(old)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a["rgba8"], b["rgba8"]) and np.array_equal(a["depth"], b["depth"])
+
+
+def test_jittered_and_shadowed_batch(api, orc):
+    s = W.bulb_1080p(30, 64, 48)
+    s["camera"]["spp"] = 3
+    s["camera"]["seed"] = 11
+    j = W.stress_julia_4k(72, 40)
+    batch = _np(api.render_batch([s, j], rgba8=True, depth=True))
+    for scene, b in zip((s, j), batch):
+        o = orc.render(scene, precision="f32", threads=THREADS)
+        res = compare(b["rgba8"].reshape(-1), b["depth"].reshape(-1), o["rgba8"], o["depth"])
+        assert res["ok"], res
+
+
+def test_batch_counters_equal_plain_counters(api):
+    scenes = small_mixed(4, seed=3)
+    import torch
+
+    for s in scenes:
+        p = api.render(s, rgba8=False, depth=False, stats=True)
+        b = api.render_batch([s], rgba8=False, depth=False, stats=True)[0]
+        torch.cuda.synchronize()
+        assert np.array_equal(p["stats"].cpu().numpy(), b["stats"].cpu().numpy())
+
+
+def test_batch_errors(api):
+    import torch
+
+    from paper_2102_01747_gb300 import _ffi as F
+
+    scenes = small_mixed(3)
+    outs = [api.alloc_image(s) for s in scenes]
+    arr = api.request_array(scenes, outs)
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    assert F.fr_render_batch(arr, 3, ws.data_ptr(), 16, None) == F.FR_ENOMEM
+    assert F.fr_render_batch(arr, 3, ws.data_ptr() + 8, 1000, None) == F.FR_EINVAL
+    assert F.fr_render_batch(arr, 0, ws.data_ptr(), 1024, None) == F.FR_EINVAL
+    arr[1].kind = 9
+    assert F.fr_render_batch(arr, 3, ws.data_ptr(), 1024, None) == F.FR_EINVAL
+    assert "request 1" in F.fr_last_error()
