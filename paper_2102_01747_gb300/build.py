@@ -30,9 +30,10 @@ def nvcc() -> str:
 
 
 def cflags() -> list:
+    extra = os.environ.get("FR_NVCC_FLAGS", "").split()  # e.g. -DFR_PERSIST_MIN_BLOCKS=3
     return ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-I", INCLUDE,
             "-Xcompiler", "-fPIC,-fvisibility=hidden,-ffp-contract=off",
-            "-Xptxas", "-warn-spills"]
+            "-Xptxas", "-warn-spills", *extra]
 
 
 def _sources():
@@ -46,6 +47,9 @@ def _deps():
 
 def stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    stamp = LIB + ".flags"
+    if (open(stamp).read() if os.path.exists(stamp) else "") != " ".join(cflags()):
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(p) > t for p in _deps())
@@ -80,6 +84,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(LIB + ".flags", "w") as f:
+        f.write(" ".join(cflags()))
     return LIB
 
 

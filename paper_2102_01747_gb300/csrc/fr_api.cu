@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 256, 0, 8, 1};
+fr_tuning g_tuning = {128, 1, 256, 0, 8, 4};
 
 fr_tuning tuning()
 {
@@ -122,12 +122,13 @@ fr_status resolve_bulb(fr::DevReq &R, const fr_bulb_params *P)
                          P->normal_mode, P->normal_h);
 }
 
+// camera, light, plane and (when out != NULL) the output buffers
 fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam, const fr_light *li,
-                         const fr_image *out)
+                         const fr_image *out, bool need_out = true)
 {
     if (!cam) return fail(FR_EINVAL, "camera is NULL");
     if (!li) return fail(FR_EINVAL, "light is NULL");
-    if (!out) return fail(FR_EINVAL, "image is NULL");
+    if (need_out && !out) return fail(FR_EINVAL, "image is NULL");
     if (cam->width < 1 || cam->height < 1) return fail(FR_EINVAL, "image %dx%d is empty", cam->width, cam->height);
     if (cam->spp < 1 || cam->spp > 64) return fail(FR_EINVAL, "spp %d outside 1..64", cam->spp);
     if ((long long)cam->width * cam->height * cam->spp >= (1LL << 31))
@@ -182,6 +183,7 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
         R.plane_hat = f4(n);
     }
 
+    if (!need_out) return FR_OK;
     if (!out->rgba8 && !out->rgba && !out->depth && !out->saved && !out->stats)
         return fail(FR_EINVAL, "image has no output buffer");
     if (!aligned(out->rgba8, 4) || !aligned(out->depth, 4) || !aligned(out->rgba, 16) ||
@@ -325,9 +327,29 @@ FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plan
                                     const fr_camera *camera, const fr_light *light, const float *saved,
                                     const float *d_rgba, const float *d_depth, float *grad, void *stream)
 {
-    (void)params; (void)plane; (void)camera; (void)light; (void)saved; (void)d_rgba; (void)d_depth;
-    (void)grad; (void)stream;
-    return fail(FR_ENOTIMPL, "fr_render_backward not built yet");
+    fr::BwdArgs A;
+    std::memset(&A, 0, sizeof A);
+    fr_status st = resolve_julia(A.R, params);
+    if (st != FR_OK) return st;
+    if (params->max_iter > fr::kMaxBwdIter)
+        return fail(FR_EINVAL, "backward keeps at most %d orbit iterations (max_iter %d)", fr::kMaxBwdIter,
+                    params->max_iter);
+    if (!camera) return fail(FR_EINVAL, "camera is NULL");
+    if (camera->spp != 1) return fail(FR_EINVAL, "backward needs spp == 1 (got %d)", camera->spp);
+    if (!saved || !d_rgba || !grad) return fail(FR_EINVAL, "saved, d_rgba and grad must be given");
+    if (!aligned(saved, 16) || !aligned(d_rgba, 16) || !aligned(d_depth, 4) || !aligned(grad, 4))
+        return fail(FR_EINVAL, "buffer misaligned (saved/d_rgba 16 B, d_depth/grad 4 B)");
+    if ((st = resolve_common(A.R, plane, camera, light, nullptr, false)) != FR_OK) return st;
+    A.saved = reinterpret_cast<const float4 *>(saved);
+    A.d_rgba = reinterpret_cast<const float4 *>(d_rgba);
+    A.d_depth = d_depth;
+    A.grad = grad;
+    A.light_norm = std::sqrt(light->dir[0] * light->dir[0] + light->dir[1] * light->dir[1] +
+                             light->dir[2] * light->dir[2]);
+    A.plane_norm = A.R.plane_on ? std::sqrt(plane->n[0] * plane->n[0] + plane->n[1] * plane->n[1] +
+                                            plane->n[2] * plane->n[2])
+                                : 1.0f;
+    return launched(fr::launch_backward(A, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -1,0 +1,232 @@
+// fr_backward.cu -- adjoint of the Julia render by implicit differentiation.
+//
+// Forward state: the hit point x of every pixel and its flags (hit, cut face,
+// shadowed), saved by the forward kernels.  Nothing of the march is kept: the
+// march is not differentiated.  At a surface hit the march has converged onto
+// the level set of the distance estimate d(x; c) through x, so the hit depth
+// t along the unit ray rd moves with a parameter theta as
+//     dt/dtheta = -(dd/dtheta) / (grad_x d . rd)          (implicit function)
+// The normal is the normalised stencil sum g = sum_k w_k d(x + o_k) of the
+// forward pass; it moves through each tap's own dependence on c and through x.
+// Lambert shading moves through n and through L = dir/|dir|.  A cut-face hit
+// sits on the plane: t = (o - n.ro)/(n.rd), normal n/|n|.
+//
+// d and its partial derivatives with respect to the point and to c come from
+// reverse mode through the orbit of Eqs. 3-4: the orbit is recomputed from the
+// point with the forward pass's own step function (so d, and with it the
+// normal, are bit-identical to the forward pass), its iterates are kept in a
+// per-thread array, and the adjoint runs back through
+//     z_{k+1} = z_k^p + c,   |z'|^2 = prod_k p^2 |z_k|^(2(p-1)),
+//     d = 0.25 log|z_N|^2 sqrt(|z_N|^2 / |z'|^2).
+// Escape counts, hit status and shadow visibility are held fixed.
+//
+// One thread per pixel; the 11 partial sums (dc[4], dn[3], doffset, ddir[3])
+// are reduced per warp with shuffles, per block in shared memory, and added to
+// the caller's gradient with one atomicAdd per block and component.
+#include "fr_launch.h"
+#include "fr_trace.cuh"
+
+namespace fr {
+
+// transpose of the Jacobian of q -> q^2 at z, applied to yb
+__device__ __forceinline__ float4 jt_square(float4 z, float4 yb)
+{
+    const float vdy = z.y * yb.y + z.z * yb.z + z.w * yb.w;
+    return make_float4(2.0f * (z.x * yb.x + vdy), 2.0f * (z.x * yb.y - z.y * yb.x),
+                       2.0f * (z.x * yb.z - z.z * yb.x), 2.0f * (z.x * yb.w - z.w * yb.x));
+}
+
+// transpose of the Jacobian of q -> q^3 = (a^3 - 3a|v|^2, (3a^2 - |v|^2) v) at z
+__device__ __forceinline__ float4 jt_cube(float4 z, float4 yb)
+{
+    const float a = z.x;
+    const float v2 = z.y * z.y + z.z * z.z + z.w * z.w;
+    const float f = 3.0f * a * a - v2;
+    const float vdy = z.y * yb.y + z.z * yb.z + z.w * yb.w;
+    const float s = -6.0f * a * yb.x - 2.0f * vdy;  // coefficient of v in vbar
+    return make_float4((3.0f * a * a - 3.0f * v2) * yb.x + 6.0f * a * vdy, s * z.y + f * yb.y,
+                       s * z.z + f * yb.z, s * z.w + f * yb.w);
+}
+
+// d(p) with d d / d p (gx) and d d / d c (gc) by reverse mode; d as in julia_de2/3
+template <int P>
+__device__ float julia_de_grad(const DevReq &R, float3 p, float3 &gx, float4 &gc)
+{
+    float4 zs[kMaxBwdIter];
+    Orbit o;
+    julia_init(o, p, R.slice_w);
+    int n = 0;
+    for (int k = 0; k < R.max_iter; k++) {
+        zs[k] = make_float4(o.a, o.b, o.c, o.d);
+        if (P == 2)
+            julia2_step(o, R.c);
+        else
+            julia3_step(o, R.c);
+        n++;
+        if (o.m > R.esc2) break;
+    }
+    const float d = julia_dist(o);
+    const float m = o.m;
+    // d = 0.25 log(m) sqrt(m / D):  dd/dm = 0.25 sqrt(m/D) (1 + 0.5 log m) / m
+    const float dd_dm = 0.25f * sqrtf(m / o.dz) * (1.0f + 0.5f * logf(m)) / m;
+    float4 zb = make_float4(2.0f * dd_dm * o.a, 2.0f * dd_dm * o.b, 2.0f * dd_dm * o.c, 2.0f * dd_dm * o.d);
+    float4 cb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int k = n - 1; k >= 0; k--) {
+        cb.x += zb.x;
+        cb.y += zb.y;
+        cb.z += zb.z;
+        cb.w += zb.w;
+        const float4 z = zs[k];
+        float4 nb = (P == 2) ? jt_square(z, zb) : jt_cube(z, zb);
+        // |z'|^2 carries p^2 |z_k|^(2(p-1)):  dd/dz_k += -d (p-1) z_k / |z_k|^2
+        const float mk = z.x * z.x + z.y * z.y + z.z * z.z + z.w * z.w;
+        const float coef = -d * (float)(P - 1) / mk;
+        nb.x += coef * z.x;
+        nb.y += coef * z.y;
+        nb.z += coef * z.z;
+        nb.w += coef * z.w;
+        zb = nb;
+    }
+    gx = v3(zb.x, zb.y, zb.z);
+    gc = cb;
+    return d;
+}
+
+// weight vector of stencil tap k in g = sum_k w_k d_k (see tap_accum)
+__device__ __forceinline__ float3 tap_weight(int mode, float h, int k)
+{
+    if (mode == 0) {
+        return v3((k == 0 || k == 3) ? h : -h, (k >= 2) ? h : -h, (k == 1 || k == 3) ? h : -h);
+    }
+    const float s = (k & 1) ? -1.0f : 1.0f;
+    const int j = k >> 1;
+    return v3(j == 0 ? s : 0.0f, j == 1 ? s : 0.0f, j == 2 ? s : 0.0f);
+}
+
+template <int P>
+__device__ void pixel_grad(const BwdArgs &A, int px, int py, float gsum[11])
+{
+    const DevReq &R = A.R;
+    const long long idx = (long long)py * R.width + px;
+    const float4 sv = A.saved[idx];
+    const uint32_t flags = __float_as_uint(sv.w);
+    if (!(flags & kFlagHit)) return;
+    const float4 dr = A.d_rgba[idx];
+    const float W = dr.x * R.albedo.x + dr.y * R.albedo.y + dr.z * R.albedo.z;
+    const float gd = A.d_depth ? A.d_depth[idx] : 0.0f;
+    const float vis = (flags & kFlagShadow) ? 0.0f : 1.0f;
+    float3 ro, rd;
+    camera_ray(R, px, py, 0, ro, rd);
+    const float3 x = v3(sv.x, sv.y, sv.z);
+    const float3 L = v3(R.light);
+
+    if (flags & kFlagFace) {
+        const float3 nh = v3(R.plane_hat);
+        const float3 nraw = v3(R.plane);
+        const float ndl = dot3(nh, L);
+        const float act = ndl > 0.0f ? W * R.kd * vis : 0.0f;
+        const float nrd = dot3(nraw, rd);
+        gsum[4] += act * (L.x - nh.x * ndl) / A.plane_norm - gd * x.x / nrd;
+        gsum[5] += act * (L.y - nh.y * ndl) / A.plane_norm - gd * x.y / nrd;
+        gsum[6] += act * (L.z - nh.z * ndl) / A.plane_norm - gd * x.z / nrd;
+        gsum[7] += gd / nrd;
+        gsum[8] += act * (nh.x - L.x * ndl) / A.light_norm;
+        gsum[9] += act * (nh.y - L.y * ndl) / A.light_norm;
+        gsum[10] += act * (nh.z - L.z * ndl) / A.light_norm;
+        return;
+    }
+
+    float3 gx0;
+    float4 gc0;
+    const float d0 = julia_de_grad<P>(R, x, gx0, gc0);
+    (void)d0;
+    const float srd = dot3(gx0, rd);
+    const float4 dtdc = make_float4(-gc0.x / srd, -gc0.y / srd, -gc0.z / srd, -gc0.w / srd);
+
+    const int taps = R.normal_mode == 0 ? 4 : 6;
+    float grd[6];
+    float4 gck[6];
+    float3 g = v3(0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        if (k < taps) {
+            float3 gxk;
+            const float dk = julia_de_grad<P>(R, tap_point(x, R.normal_mode, R.normal_h, k), gxk, gck[k]);
+            grd[k] = dot3(gxk, rd);
+            tap_accum(g, R.normal_mode, R.normal_h, k, dk);
+        }
+    }
+    const float gl = sqrtf(dot3(g, g));
+    if (!(gl > 0.0f) || !isfinite(gl)) return;  // the forward used -rd: no gradient
+    const float3 n = v3(g.x / gl, g.y / gl, g.z / gl);
+    const float ndl = dot3(n, L);
+    const float act = ndl > 0.0f ? W * R.kd * vis : 0.0f;
+    // u = act (I - n n^T) L / |g|; dLoss/dc = sum_k (u . w_k) (gc_k + (gx_k . rd) dt/dc) + gd dt/dc
+    const float3 u = v3(act * (L.x - n.x * ndl) / gl, act * (L.y - n.y * ndl) / gl,
+                        act * (L.z - n.z * ndl) / gl);
+    float s = gd;  // coefficient of dt/dc
+    float4 gcsum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        if (k < taps) {
+            const float uw = dot3(u, tap_weight(R.normal_mode, R.normal_h, k));
+            gcsum.x += uw * gck[k].x;
+            gcsum.y += uw * gck[k].y;
+            gcsum.z += uw * gck[k].z;
+            gcsum.w += uw * gck[k].w;
+            s += uw * grd[k];
+        }
+    }
+    gsum[0] += gcsum.x + s * dtdc.x;
+    gsum[1] += gcsum.y + s * dtdc.y;
+    gsum[2] += gcsum.z + s * dtdc.z;
+    gsum[3] += gcsum.w + s * dtdc.w;
+    gsum[8] += act * (n.x - L.x * ndl) / A.light_norm;
+    gsum[9] += act * (n.y - L.y * ndl) / A.light_norm;
+    gsum[10] += act * (n.z - L.z * ndl) / A.light_norm;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) backward_kernel(const __grid_constant__ BwdArgs A)
+{
+    const DevReq &R = A.R;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tile = gtid >> 5;
+    const int lane = threadIdx.x & 31;
+    const int px = (int)(tile % R.tiles_x) * kTileW + (lane & (kTileW - 1));
+    const int py = (int)(tile / R.tiles_x) * kTileH + (lane / kTileW);
+    float gsum[11];
+#pragma unroll
+    for (int k = 0; k < 11; k++) gsum[k] = 0.0f;
+    if (px < R.width && py < R.height) pixel_grad<P>(A, px, py, gsum);
+
+    __shared__ float part[8][11];
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 11; k++) {
+        float v = gsum[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 11) {
+        float v = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += part[w][threadIdx.x];
+        if (v != 0.0f) atomicAdd(A.grad + threadIdx.x, v);
+    }
+}
+
+cudaError_t launch_backward(const BwdArgs &A, cudaStream_t s)
+{
+    const int block = 256;
+    const long long tiles_y = (A.R.height + kTileH - 1) / kTileH;
+    const long long threads = (long long)A.R.tiles_x * tiles_y * 32;
+    const long long grid = (threads + block - 1) / block;
+    if (A.R.power == 2)
+        backward_kernel<2><<<(unsigned)grid, block, 0, s>>>(A);
+    else
+        backward_kernel<3><<<(unsigned)grid, block, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace fr

@@ -219,7 +219,9 @@ __device__ __forceinline__ float julia_dist(const Orbit &o)
 // Mandelbulb (Listing "Mandelbulb distance", Eq. 1): w0 = c, dz = 1; each step
 // dz <- n r^(n-1) dz + 1 and w <- r^n (sin b sin a, cos b, sin b cos a) + c with
 // r = |w|, b = n acos(w.y / r) (y/r clamped to [-1, 1]), a = n atan2(w.x, w.z);
-// r = 0 gives the zero power.  d = 0.25 log(m) sqrt(m) / dz.
+// r = 0 gives the zero power.  d = 0.25 log(m) sqrt(m) / dz.  The integer
+// powers r^(n-1) and r^n are products (ipow) rather than two calls of the
+// general powf: the same quantities in a few multiplications.
 __device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
 {
     o.a = p.x; o.b = p.y; o.c = p.z; o.d = 0.0f;
@@ -227,11 +229,25 @@ __device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
     o.dz = 1.0f;
 }
 
+// r^k for an integer k >= 0 by binary exponentiation (exact-arithmetic power;
+// each product is rounded once, so r^8 carries at most 3 roundings)
+__device__ __forceinline__ float ipow(float r, int k)
+{
+    float res = 1.0f, b = r;
+    while (k > 0) {
+        if (k & 1) res *= b;
+        k >>= 1;
+        if (k) b *= b;
+    }
+    return res;
+}
+
 __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
 {
     const float nf = (float)n;
     const float r = sqrtf(o.m);
-    o.dz = nf * powf(r, nf - 1.0f) * o.dz + 1.0f;
+    const float rn1 = ipow(r, n - 1);  // r^(n-1) (the listing's pow(sqrt(m), n-1))
+    o.dz = nf * rn1 * o.dz + 1.0f;
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
         const float ct = fminf(fmaxf(o.b / r, -1.0f), 1.0f);
@@ -240,7 +256,7 @@ __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
         float sb, cb, sa, ca;
         sincosf(b, &sb, &cb);
         sincosf(a, &sa, &ca);
-        const float rn = powf(r, nf);
+        const float rn = rn1 * r;  // r^n (the listing's pow(r, n))
         px = rn * (sb * sa);
         py = rn * cb;
         pz = rn * (sb * ca);

@@ -19,6 +19,22 @@ struct BatchArgs {
     DevReq reqs[kMaxReqPerLaunch];
 };
 
+// orbit iterations the adjoint keeps per DE (max_iter of a backward call)
+constexpr int kMaxBwdIter = 64;
+
+struct BwdArgs {
+    DevReq R;                // the forward request (Julia)
+    const float4 *saved;     // hit point + flags per pixel
+    const float4 *d_rgba;    // cotangent of the float colour
+    const float *d_depth;    // cotangent of the depth, may be NULL
+    float *grad;             // 11 floats, accumulated
+    float light_norm;        // |light dir| as given (before normalisation)
+    float plane_norm;        // |plane n| as given
+};
+
+// adjoint of one Julia render (one thread per pixel, block reduction, atomics)
+cudaError_t launch_backward(const BwdArgs &A, cudaStream_t s);
+
 // one-ray-per-thread forward kernel for one request
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s);
 

@@ -253,8 +253,13 @@ __device__ __forceinline__ void start_pixel(Lane &S, long long u, const DevReq *
     begin_samples<COUNT>(S, R, pc);
 }
 
+// resident 256-thread CTAs the register budget is fitted to (3 -> <= 85 registers, 24 warps per SM)
+#ifndef FR_PERSIST_MIN_BLOCKS
+#define FR_PERSIST_MIN_BLOCKS 2
+#endif
+
 template <int KJ, bool COUNT>
-__global__ void __launch_bounds__(256) persist_kernel(const __grid_constant__ BatchArgs A)
+__global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(const __grid_constant__ BatchArgs A)
 {
     extern __shared__ float4 smem[];
     DevReq *sreq = reinterpret_cast<DevReq *>(smem);
