@@ -80,7 +80,7 @@ enum {
 typedef struct {
     float eye[3], target[3], up[3];
     float fov_y_deg;
-    int32_t width, height;   /* >= 1, width*height*spp < 2^31          */
+    int32_t width, height;   /* 1..65535, width*height*spp < 2^31      */
     int32_t spp;             /* samples per pixel, 1..64               */
     uint32_t seed;           /* jitter seed (used when spp > 1)        */
 } fr_camera;
@@ -166,7 +166,8 @@ typedef struct {
     int32_t persist_block;       /* threads per block of the persistent kernel          */
     int32_t persist_ctas_per_sm; /* resident CTAs per SM; 0 = as many as fit            */
     int32_t refill_threshold;    /* refill a warp once this many lanes are idle (1..32) */
-    int32_t persist_unroll;      /* orbit-loop unroll depth of the persistent kernel    */
+    int32_t persist_unroll;      /* Julia orbit steps per scheduling round: 1, 2, 4, 8  */
+    int32_t queue_chunk;         /* pixels a warp reserves per queue atomic (32..4096, x32) */
 } fr_tuning;
 
 /* Render one quaternion Julia image with the one-ray-per-thread kernel

@@ -40,6 +40,7 @@ class JuliaRender(torch.autograd.Function):
         ctx.scene = s
         ctx.save_for_backward(out["saved"])
         ctx.dev = out["rgba"].device
+        ctx.in_dev = (c.device, plane_n.device, plane_o.device, light_dir.device)
         return out["rgba"], out["depth"]
 
     @staticmethod
@@ -56,7 +57,8 @@ class JuliaRender(torch.autograd.Function):
                                   None if dd is None else dd.data_ptr(), grad.data_ptr(),
                                   api.current_stream(ctx.dev))
         F.check(st)
-        return grad[0:4], grad[4:7], grad[7:8], grad[8:11], None
+        dc, dn, do, dl = ctx.in_dev
+        return grad[0:4].to(dc), grad[4:7].to(dn), grad[7:8].to(do), grad[8:11].to(dl), None
 
 
 def julia_render(scene, c, plane_n, plane_o, light_dir):

@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 256, 0, 8, 4};
+fr_tuning g_tuning = {128, 1, 128, 0, 4, 4, 64};
 
 fr_tuning tuning()
 {
@@ -130,6 +130,8 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
     if (!li) return fail(FR_EINVAL, "light is NULL");
     if (need_out && !out) return fail(FR_EINVAL, "image is NULL");
     if (cam->width < 1 || cam->height < 1) return fail(FR_EINVAL, "image %dx%d is empty", cam->width, cam->height);
+    if (cam->width > 65535 || cam->height > 65535)
+        return fail(FR_EINVAL, "image sides are limited to 65535 (got %dx%d)", cam->width, cam->height);
     if (cam->spp < 1 || cam->spp > 64) return fail(FR_EINVAL, "spp %d outside 1..64", cam->spp);
     if ((long long)cam->width * cam->height * cam->spp >= (1LL << 31))
         return fail(FR_EINVAL, "width*height*spp must stay below 2^31");
@@ -226,8 +228,10 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
     auto unroll_ok = [](int u) { return u == 1 || u == 2 || u == 4; };
     if (!block_ok(t->plain_block) || !block_ok(t->persist_block))
         return fail(FR_EINVAL, "block sizes must be multiples of 32 in 32..256");
-    if (!unroll_ok(t->plain_unroll) || !unroll_ok(t->persist_unroll))
-        return fail(FR_EINVAL, "unroll depth must be 1, 2 or 4");
+    if (!unroll_ok(t->plain_unroll) || !(unroll_ok(t->persist_unroll) || t->persist_unroll == 8))
+        return fail(FR_EINVAL, "unroll depth must be 1, 2 or 4 (persistent: also 8)");
+    if (t->queue_chunk < 32 || t->queue_chunk > 4096 || t->queue_chunk % 32)
+        return fail(FR_EINVAL, "queue_chunk must be a multiple of 32 in 32..4096");
     if (t->persist_ctas_per_sm < 0 || t->persist_ctas_per_sm > 32)
         return fail(FR_EINVAL, "persist_ctas_per_sm outside 0..32");
     if (t->refill_threshold < 1 || t->refill_threshold > 32)
@@ -315,6 +319,7 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         A.n_reqs = n;
         A.total_units = units;
         A.refill_threshold = tu.refill_threshold;
+        A.chunk = tu.queue_chunk;
         A.queue = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 256 * (size_t)chunk);
         const fr_status st = launched(fr::launch_persist(A, tu.persist_block, tu.persist_ctas_per_sm,
                                                          tu.persist_unroll, count, (cudaStream_t)stream));

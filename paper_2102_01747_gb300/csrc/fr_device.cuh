@@ -77,19 +77,31 @@ struct __align__(16) DevReq {
     long long n_units;    // tiles * 32
 };
 
+// ------------------------------------------------------------------ arithmetic
+// Every rounding step below is spelled out (fmaf = one fused multiply-add,
+// __fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn = one rounded operation that
+// the compiler may not fuse).  Left to itself the compiler fuses a*b + c
+// depending on the surrounding code, so the same function inlined into two
+// kernels could round differently; written out, every kernel that calls these
+// routines computes bit-identical values for the same ray.
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float dvd(float a, float b) { return __fdiv_rn(a, b); }
+
 // ------------------------------------------------------------------ vectors
 __device__ __forceinline__ float3 v3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float3 v3(float4 a) { return make_float3(a.x, a.y, a.z); }
-__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 operator*(float3 a, float s) { return v3(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float dot3(float3 a, float3 b)
+{
+    return fmaf(a.z, b.z, fmaf(a.y, b.y, mul(a.x, b.x)));
+}
 __device__ __forceinline__ float3 normalize3(float3 a)
 {
-    float l = sqrtf(dot3(a, a));
-    return v3(a.x / l, a.y / l, a.z / l);
+    const float l = sqrtf(dot3(a, a));
+    return v3(dvd(a.x, l), dvd(a.y, l), dvd(a.z, l));
 }
-// ro + t * rd, one FFMA per component
+// ro + t * rd
 __device__ __forceinline__ float3 along(float3 ro, float3 rd, float t)
 {
     return v3(fmaf(rd.x, t, ro.x), fmaf(rd.y, t, ro.y), fmaf(rd.z, t, ro.z));
@@ -119,11 +131,13 @@ __device__ __forceinline__ void camera_ray(const DevReq &R, int px, int py, int 
         sx = (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f);
         sy = (float)(uint32_t)((h >> 16) & 0xffffffULL) * (1.0f / 16777216.0f);
     }
-    float uu = ((float)px + sx) * R.inv_w;
-    float vv = ((float)py + sy) * R.inv_h;
-    float ax = (2.0f * uu - 1.0f) * R.th_aspect;
-    float ay = (1.0f - 2.0f * vv) * R.th;
-    rd = normalize3(v3(R.fwd) + v3(R.right) * ax + v3(R.up) * ay);
+    const float uu = mul(add((float)px, sx), R.inv_w);
+    const float vv = mul(add((float)py, sy), R.inv_h);
+    const float ax = mul(fmaf(2.0f, uu, -1.0f), R.th_aspect);
+    const float ay = mul(fmaf(-2.0f, vv, 1.0f), R.th);
+    rd = normalize3(v3(fmaf(R.up.x, ay, fmaf(R.right.x, ax, R.fwd.x)),
+                       fmaf(R.up.y, ay, fmaf(R.right.y, ax, R.fwd.y)),
+                       fmaf(R.up.z, ay, fmaf(R.right.z, ax, R.fwd.z))));
     ro = v3(R.eye);
 }
 
@@ -134,22 +148,22 @@ __device__ __forceinline__ void camera_ray(const DevReq &R, int px, int py, int 
 __device__ __forceinline__ bool bounds(const DevReq &R, float3 ro, float3 rd, float &t0, float &t1,
                                        bool &from_plane)
 {
-    float b = dot3(ro, rd);
-    float cc = dot3(ro, ro) - R.bound_r2;
-    float disc = b * b - cc;
+    const float b = dot3(ro, rd);
+    const float cc = sub(dot3(ro, ro), R.bound_r2);
+    const float disc = fmaf(b, b, -cc);
     if (!(disc >= 0.0f)) return false;
-    float s = sqrtf(disc);
-    t0 = fmaxf(-b - s, R.eps);
-    t1 = fminf(-b + s, 7000.0f);
+    const float s = sqrtf(disc);
+    t0 = fmaxf(sub(-b, s), R.eps);
+    t1 = fminf(sub(s, b), 7000.0f);
     from_plane = false;
     if (R.plane_on) {
-        float3 n = v3(R.plane);
-        float a = dot3(n, ro) - R.plane.w;
-        float bb = dot3(n, rd);
+        const float3 n = v3(R.plane);
+        const float a = sub(dot3(n, ro), R.plane.w);
+        const float bb = dot3(n, rd);
         if (bb == 0.0f) {
             if (a > 0.0f) return false;
         } else {
-            float ts = -a / bb;
+            const float ts = dvd(-a, bb);
             if (bb > 0.0f) {
                 t1 = fminf(t1, ts);
             } else if (ts > t0) {
@@ -176,44 +190,50 @@ struct Orbit {
     float m;           // |z|^2 (|w|^2) of the current iterate
 };
 
+__device__ __forceinline__ float norm2_4(float a, float b, float c, float d)
+{
+    return fmaf(d, d, fmaf(c, c, fmaf(b, b, mul(a, a))));
+}
+
 __device__ __forceinline__ void julia_init(Orbit &o, float3 p, float slice_w)
 {
     o.a = p.x; o.b = p.y; o.c = p.z; o.d = slice_w;
-    o.m = o.a * o.a + o.b * o.b + o.c * o.c + o.d * o.d;
+    o.m = norm2_4(o.a, o.b, o.c, o.d);
     o.dz = 1.0f;
 }
 
 // degree 2: z^2 = (x^2 - |v|^2, 2 x v) for z = (x, v); |z'|^2 *= 4 |z|^2
 __device__ __forceinline__ void julia2_step(Orbit &o, const float4 c)
 {
-    o.dz *= 4.0f * o.m;
-    const float tx = o.a + o.a;
-    const float nx = o.a * o.a - (o.b * o.b + o.c * o.c + o.d * o.d) + c.x;
-    o.b = tx * o.b + c.y;
-    o.c = tx * o.c + c.z;
-    o.d = tx * o.d + c.w;
+    o.dz = mul(o.dz, mul(4.0f, o.m));
+    const float tx = add(o.a, o.a);
+    const float v2 = fmaf(o.d, o.d, fmaf(o.c, o.c, mul(o.b, o.b)));
+    const float nx = add(fmaf(o.a, o.a, -v2), c.x);
+    o.b = fmaf(tx, o.b, c.y);
+    o.c = fmaf(tx, o.c, c.z);
+    o.d = fmaf(tx, o.d, c.w);
     o.a = nx;
-    o.m = o.a * o.a + o.b * o.b + o.c * o.c + o.d * o.d;
+    o.m = norm2_4(o.a, o.b, o.c, o.d);
 }
 
 // degree 3 (the listing's cube): z^3 = (x^3 - 3x|v|^2, (3x^2 - |v|^2) v); |z'|^2 *= 9 |z|^4
 __device__ __forceinline__ void julia3_step(Orbit &o, const float4 c)
 {
-    o.dz *= 9.0f * (o.m * o.m);
-    const float x2 = o.a * o.a;
-    const float v2 = o.b * o.b + o.c * o.c + o.d * o.d;
-    const float f = 3.0f * x2 - v2;
-    const float nx = o.a * (x2 - 3.0f * v2) + c.x;
-    o.b = f * o.b + c.y;
-    o.c = f * o.c + c.z;
-    o.d = f * o.d + c.w;
+    o.dz = mul(o.dz, mul(9.0f, mul(o.m, o.m)));
+    const float x2 = mul(o.a, o.a);
+    const float v2 = fmaf(o.d, o.d, fmaf(o.c, o.c, mul(o.b, o.b)));
+    const float f = fmaf(3.0f, x2, -v2);
+    const float nx = fmaf(o.a, fmaf(-3.0f, v2, x2), c.x);
+    o.b = fmaf(f, o.b, c.y);
+    o.c = fmaf(f, o.c, c.z);
+    o.d = fmaf(f, o.d, c.w);
     o.a = nx;
-    o.m = o.a * o.a + o.b * o.b + o.c * o.c + o.d * o.d;
+    o.m = norm2_4(o.a, o.b, o.c, o.d);
 }
 
 __device__ __forceinline__ float julia_dist(const Orbit &o)
 {
-    return 0.25f * logf(o.m) * sqrtf(o.m / o.dz);
+    return mul(mul(0.25f, logf(o.m)), sqrtf(dvd(o.m, o.dz)));
 }
 
 // Mandelbulb (Listing "Mandelbulb distance", Eq. 1): w0 = c, dz = 1; each step
@@ -225,19 +245,19 @@ __device__ __forceinline__ float julia_dist(const Orbit &o)
 __device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
 {
     o.a = p.x; o.b = p.y; o.c = p.z; o.d = 0.0f;
-    o.m = o.a * o.a + o.b * o.b + o.c * o.c;
+    o.m = dot3(p, p);
     o.dz = 1.0f;
 }
 
-// r^k for an integer k >= 0 by binary exponentiation (exact-arithmetic power;
-// each product is rounded once, so r^8 carries at most 3 roundings)
+// r^k for an integer k >= 0 by binary exponentiation (each product rounded
+// once, so r^7 carries at most 4 roundings)
 __device__ __forceinline__ float ipow(float r, int k)
 {
     float res = 1.0f, b = r;
     while (k > 0) {
-        if (k & 1) res *= b;
+        if (k & 1) res = mul(res, b);
         k >>= 1;
-        if (k) b *= b;
+        if (k) b = mul(b, b);
     }
     return res;
 }
@@ -247,29 +267,29 @@ __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
     const float nf = (float)n;
     const float r = sqrtf(o.m);
     const float rn1 = ipow(r, n - 1);  // r^(n-1) (the listing's pow(sqrt(m), n-1))
-    o.dz = nf * rn1 * o.dz + 1.0f;
+    o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
-        const float ct = fminf(fmaxf(o.b / r, -1.0f), 1.0f);
-        const float b = nf * acosf(ct);
-        const float a = nf * atan2f(o.a, o.c);
+        const float ct = fminf(fmaxf(dvd(o.b, r), -1.0f), 1.0f);
+        const float b = mul(nf, acosf(ct));
+        const float a = mul(nf, atan2f(o.a, o.c));
         float sb, cb, sa, ca;
         sincosf(b, &sb, &cb);
         sincosf(a, &sa, &ca);
-        const float rn = rn1 * r;  // r^n (the listing's pow(r, n))
-        px = rn * (sb * sa);
-        py = rn * cb;
-        pz = rn * (sb * ca);
+        const float rn = mul(rn1, r);  // r^n (the listing's pow(r, n))
+        px = mul(rn, mul(sb, sa));
+        py = mul(rn, cb);
+        pz = mul(rn, mul(sb, ca));
     }
-    o.a = px + cpt.x;
-    o.b = py + cpt.y;
-    o.c = pz + cpt.z;
-    o.m = o.a * o.a + o.b * o.b + o.c * o.c;
+    o.a = add(px, cpt.x);
+    o.b = add(py, cpt.y);
+    o.c = add(pz, cpt.z);
+    o.m = dot3(v3(o.a, o.b, o.c), v3(o.a, o.b, o.c));
 }
 
 __device__ __forceinline__ float bulb_dist(const Orbit &o)
 {
-    return 0.25f * logf(o.m) * sqrtf(o.m) / o.dz;
+    return dvd(mul(mul(0.25f, logf(o.m)), sqrtf(o.m)), o.dz);
 }
 
 // whole-orbit DEs (one-ray-per-thread kernel); trips = orbit loop trips
@@ -345,10 +365,10 @@ __device__ __forceinline__ float3 tap_point(float3 x, int mode, float h, int k)
         const float sx = (k == 0 || k == 3) ? h : -h;
         const float sy = (k >= 2) ? h : -h;
         const float sz = (k == 1 || k == 3) ? h : -h;
-        return v3(x.x + sx, x.y + sy, x.z + sz);
+        return v3(add(x.x, sx), add(x.y, sy), add(x.z, sz));
     }
     const float s = (k & 1) ? -h : h;
-    return v3(x.x + (k < 2 ? s : 0.0f), x.y + ((k >> 1) == 1 ? s : 0.0f), x.z + (k >= 4 ? s : 0.0f));
+    return v3(k < 2 ? add(x.x, s) : x.x, (k >> 1) == 1 ? add(x.y, s) : x.y, k >= 4 ? add(x.z, s) : x.z);
 }
 
 __device__ __forceinline__ void tap_accum(float3 &g, int mode, float h, int k, float d)
@@ -364,40 +384,66 @@ __device__ __forceinline__ void tap_accum(float3 &g, int mode, float h, int k, f
     }
     const int j = k >> 1;
     if (j == 0)
-        g.x = (k & 1) ? g.x - d : d;
+        g.x = (k & 1) ? sub(g.x, d) : d;
     else if (j == 1)
-        g.y = (k & 1) ? g.y - d : d;
+        g.y = (k & 1) ? sub(g.y, d) : d;
     else
-        g.z = (k & 1) ? g.z - d : d;
+        g.z = (k & 1) ? sub(g.z, d) : d;
 }
 
 // unit gradient, -rd when it is zero or not finite
 __device__ __forceinline__ float3 finish_normal(float3 g, float3 rd)
 {
     const float l = sqrtf(dot3(g, g));
-    if (!(l > 0.0f) || !isfinite(l)) return rd * -1.0f;
-    return v3(g.x / l, g.y / l, g.z / l);
+    if (!(l > 0.0f) || !isfinite(l)) return v3(-rd.x, -rd.y, -rd.z);
+    return v3(dvd(g.x, l), dvd(g.y, l), dvd(g.z, l));
+}
+
+// shadow-ray origin x + off n
+__device__ __forceinline__ float3 offset_point(float3 x, float3 n, float off)
+{
+    return v3(fmaf(n.x, off, x.x), fmaf(n.y, off, x.y), fmaf(n.z, off, x.z));
 }
 
 // ------------------------------------------------------------------ shading
 __device__ __forceinline__ float4 shade(const DevReq &R, float3 n, float vis)
 {
-    float ndl = dot3(n, v3(R.light));
-    float diff = ndl > 0.0f ? ndl : 0.0f;
-    float k = R.ka + R.kd * diff * vis;
-    return make_float4(R.albedo.x * k, R.albedo.y * k, R.albedo.z * k, 1.0f);
+    const float ndl = dot3(n, v3(R.light));
+    const float diff = ndl > 0.0f ? ndl : 0.0f;
+    const float k = fmaf(mul(R.kd, diff), vis, R.ka);
+    return make_float4(mul(R.albedo.x, k), mul(R.albedo.y, k), mul(R.albedo.z, k), 1.0f);
 }
 
 // round-half-up of clamp(x, 0, 1) * 255 (NaN -> 0)
 __device__ __forceinline__ uint32_t quantize(float x)
 {
-    float y = fminf(fmaxf(x, 0.0f), 1.0f);
-    return (uint32_t)floorf(__fadd_rn(__fmul_rn(y, 255.0f), 0.5f));
+    const float y = fminf(fmaxf(x, 0.0f), 1.0f);
+    return (uint32_t)floorf(add(mul(y, 255.0f), 0.5f));
 }
 
 __device__ __forceinline__ uint32_t pack_rgba8(float4 c)
 {
     return quantize(c.x) | (quantize(c.y) << 8) | (quantize(c.z) << 16) | (quantize(c.w) << 24);
+}
+
+// running sum over samples and the mean
+__device__ __forceinline__ void acc4(float4 &acc, float4 c)
+{
+    acc.x = add(acc.x, c.x);
+    acc.y = add(acc.y, c.y);
+    acc.z = add(acc.z, c.z);
+    acc.w = add(acc.w, c.w);
+}
+__device__ __forceinline__ float4 mean4(float4 acc, int spp)
+{
+    const float fs = (float)spp;
+    return make_float4(dvd(acc.x, fs), dvd(acc.y, fs), dvd(acc.z, fs), dvd(acc.w, fs));
+}
+
+// march update t += min(d, max_step)
+__device__ __forceinline__ float march_step(float t, float d, float max_step)
+{
+    return add(t, (d < max_step) ? d : max_step);
 }
 
 // per-thread event counters (only kept in the counting kernels)

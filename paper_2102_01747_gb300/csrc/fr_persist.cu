@@ -3,26 +3,29 @@
 // Why: in the one-ray-per-thread kernel a warp runs until its slowest lane is
 // done, twice over: rays need 1..max_steps march steps, and every DE call
 // needs 1..max_iter orbit steps (Mandelbulb 1080p: 2.7 on average, up to 12).
-// Measured on that kernel: 10 of 32 lanes active per issued instruction and a
-// long tail of nearly empty SMs.
+// Measured on that kernel at 1080p: 16 of 32 lanes active per issued
+// instruction; on a batch of small images every launch is as long as its
+// slowest pixel.
 //
 // How: CTAs stay resident (grid = SMs x resident CTAs).  Each lane holds one
-// pixel's complete state: its sample, the phase of the current ray (camera
-// march, normal taps, shadow march), the march variables and one orbit in
-// progress.  Every round of the warp loop advances each lane's orbit by a few
-// steps (Julia: the unroll depth K, Mandelbulb: one); a lane whose orbit has
-// escaped or reached max_iter turns it into a distance (Eq. 2), feeds it to
-// its ray's state machine (march step, normal tap or shadow step, Listing
-// "Julia Set ray cast") and starts its next orbit right away, so lanes never
-// wait for each other's orbits or rays.  A finished pixel is stored and its
-// lane refilled from one queue over every pixel of every request: once
-// `refill_threshold` lanes are idle the warp takes that many pixels with a
-// single atomicAdd and hands them out by ballot rank.  A warp is short of work
-// only at the very end of the queue.
+// pixel's complete state (packed into few registers): its sample, the phase of
+// the current ray (camera march, normal taps, shadow march), the march
+// variables and one orbit in progress.  Every round of the warp loop advances
+// each busy lane's orbit by a few steps (Julia: the unroll depth K, Mandelbulb:
+// one); a lane whose orbit has escaped or reached max_iter turns it into a
+// distance (Eq. 2), feeds it to its ray's state machine (march step, normal
+// tap or shadow step, Listing "Julia Set ray cast") and starts its next orbit
+// at once, so lanes never wait for each other's orbits or rays.  A finished
+// pixel is stored and its lane refilled from one queue over every pixel of
+// every request.  Each warp reserves `chunk` pixels at a time with a single
+// atomicAdd on the queue head and hands them to its idle lanes by ballot rank
+// once `refill_threshold` lanes are idle; the reservation keeps the atomics
+// on the one queue head rare (they serialise in L2).
 //
 // The orbit steps, the distance, the march update and the stencils are the
-// same device functions the one-ray-per-thread kernel uses, in the same order
-// per ray, so both kernels produce the same image.
+// same device functions, with every rounding step spelled out, that the
+// one-ray-per-thread kernel uses, in the same order per ray, so the two
+// kernels produce bit-identical images.
 //
 // The request table (<= 64 DevReq) travels in the kernel parameters
 // (__grid_constant__) and is staged into shared memory by every CTA, since the
@@ -34,52 +37,83 @@
 
 namespace fr {
 
-enum : int { PH_IDLE = 0, PH_PRIMARY = 1, PH_NORMAL = 2, PH_SHADOW = 3 };
+enum : uint32_t { PH_IDLE = 0, PH_PRIMARY = 1, PH_NORMAL = 2, PH_SHADOW = 3 };
 
+// Lane state.  Small integers are packed:
+//   pix  = px | py << 16
+//   meta = req (bits 0-7) | phase (8-9) | tap (10-12) | fp (13) | sample (14-20)
+//          | sample flags (21-23) | pixel flags (24-26)
+//   cnt  = orbit steps of the current DE (bits 0-10) | march steps (11-30)
+// During the normal phase `ro` holds the current stencil tap point (the camera
+// ray's origin is no longer needed there).
 struct Lane {
-    int req;          // request index (shared-memory table)
-    int px, py, sample;
-    int phase;
-    int steps;        // DE calls of the current march
-    int tap;          // current stencil tap
-    int it;           // orbit steps of the current DE
-    bool fp;          // march interval starts on the cut plane
+    uint32_t pix, meta, cnt;
     float3 ro, rd;
-    float t, t1;
-    float thit;       // depth of the current sample's camera-ray hit
+    float t, t1, thit;
     float3 x;         // hit point of the current sample
     float3 g;         // stencil sum, then the unit normal
-    float3 cpt;       // point of the current DE (the Mandelbulb's c)
     Orbit o;
-    uint32_t sflags;  // flags of the current sample
     float4 acc;       // colour summed over samples
     float dmin;       // nearest hit over samples
-    float3 xbest;
-    uint32_t pflags;  // flags ORed over samples
 };
+
+__device__ __forceinline__ uint32_t L_req(const Lane &S) { return S.meta & 0xffu; }
+__device__ __forceinline__ uint32_t L_phase(const Lane &S) { return (S.meta >> 8) & 3u; }
+__device__ __forceinline__ void L_set_phase(Lane &S, uint32_t p) { S.meta = (S.meta & ~(3u << 8)) | (p << 8); }
+__device__ __forceinline__ int L_tap(const Lane &S) { return (int)((S.meta >> 10) & 7u); }
+__device__ __forceinline__ void L_set_tap(Lane &S, int k) { S.meta = (S.meta & ~(7u << 10)) | ((uint32_t)k << 10); }
+__device__ __forceinline__ bool L_fp(const Lane &S) { return (S.meta >> 13) & 1u; }
+__device__ __forceinline__ void L_set_fp(Lane &S, bool f) { S.meta = (S.meta & ~(1u << 13)) | ((uint32_t)f << 13); }
+__device__ __forceinline__ int L_sample(const Lane &S) { return (int)((S.meta >> 14) & 127u); }
+__device__ __forceinline__ void L_set_sample(Lane &S, int k) { S.meta = (S.meta & ~(127u << 14)) | ((uint32_t)k << 14); }
+__device__ __forceinline__ uint32_t L_sflags(const Lane &S) { return (S.meta >> 21) & 7u; }
+__device__ __forceinline__ void L_set_sflags(Lane &S, uint32_t f) { S.meta = (S.meta & ~(7u << 21)) | (f << 21); }
+__device__ __forceinline__ uint32_t L_pflags(const Lane &S) { return (S.meta >> 24) & 7u; }
+__device__ __forceinline__ int L_px(const Lane &S) { return (int)(S.pix & 0xffffu); }
+__device__ __forceinline__ int L_py(const Lane &S) { return (int)(S.pix >> 16); }
+__device__ __forceinline__ int L_it(const Lane &S) { return (int)(S.cnt & 0x7ffu); }
+__device__ __forceinline__ int L_steps(const Lane &S) { return (int)(S.cnt >> 11); }
 
 // per-pixel counters of the counting variant, flushed when the pixel is stored
 struct PixCount {
     unsigned long long v[kNStats];
 };
 
+// start a DE at p (the Mandelbulb's c is p; kept in `ro` for the normal taps,
+// recomputed as ro + t rd during a march)
 __device__ __forceinline__ void begin_de(Lane &S, const DevReq &R, float3 p)
 {
-    S.cpt = p;
-    S.it = 0;
+    S.cnt &= ~0x7ffu;
     if (R.kind == 0)
         julia_init(S.o, p, R.slice_w);
     else
         bulb_init(S.o, p);
 }
 
+__device__ __forceinline__ long long pixel_index(const DevReq &R, const Lane &S)
+{
+    return (long long)L_py(S) * R.width + L_px(S);
+}
+
 template <bool COUNT>
 __device__ __forceinline__ void store_and_idle(Lane &S, const DevReq &R, PixCount &pc)
 {
-    const float fs = (float)R.spp;
-    const float4 acc = make_float4(S.acc.x / fs, S.acc.y / fs, S.acc.z / fs, S.acc.w / fs);
-    store_pixel(R, S.px, S.py, acc, S.dmin, S.xbest, S.pflags);
-    S.phase = PH_IDLE;
+    const long long idx = pixel_index(R, S);
+    const float4 c = mean4(S.acc, R.spp);
+    if (R.rgba8) R.rgba8[idx] = pack_rgba8(c);
+    if (R.rgba) R.rgba[idx] = c;
+    if (R.depth) R.depth[idx] = S.dmin;
+    if (R.saved) {
+        // the hit point of the nearest sample was written when it was found
+        float *sv = reinterpret_cast<float *>(R.saved + idx);
+        if (!(L_pflags(S) & kFlagHit)) {
+            sv[0] = 0.0f;
+            sv[1] = 0.0f;
+            sv[2] = 0.0f;
+        }
+        sv[3] = __uint_as_float(L_pflags(S));
+    }
+    L_set_phase(S, PH_IDLE);
     if (COUNT && R.stats) {
 #pragma unroll
         for (int k = 0; k < kNStats; k++)
@@ -87,53 +121,55 @@ __device__ __forceinline__ void store_and_idle(Lane &S, const DevReq &R, PixCoun
     }
 }
 
-// Start samples S.sample.. of the lane's pixel until one needs a DE; samples
+// Start samples sample.. of the lane's pixel until one needs a DE; samples
 // whose ray misses the search interval take the background.  When no sample
 // is left the pixel is stored and the lane goes idle.
 template <bool COUNT>
 __device__ void begin_samples(Lane &S, const DevReq &R, PixCount &pc)
 {
-    while (S.sample < R.spp) {
+    int sample = L_sample(S);
+    while (sample < R.spp) {
         float3 ro, rd;
-        camera_ray(R, S.px, S.py, S.sample, ro, rd);
+        camera_ray(R, L_px(S), L_py(S), sample, ro, rd);
         if (COUNT) pc.v[kStatPrimaryRays] += 1;
         float t0, t1;
         bool fp;
         if (bounds(R, ro, rd, t0, t1, fp)) {
-            S.phase = PH_PRIMARY;
+            L_set_sample(S, sample);
+            L_set_phase(S, PH_PRIMARY);
+            L_set_fp(S, fp);
+            S.cnt = 0;
             S.ro = ro;
             S.rd = rd;
             S.t = t0;
             S.t1 = t1;
-            S.fp = fp;
-            S.steps = 0;
             begin_de(S, R, along(ro, rd, t0));
             return;
         }
-        S.acc.x += R.bg.x;
-        S.acc.y += R.bg.y;
-        S.acc.z += R.bg.z;
-        S.acc.w += R.bg.w;
-        S.sample++;
+        acc4(S.acc, R.bg);
+        sample++;
     }
+    L_set_sample(S, sample);
     store_and_idle<COUNT>(S, R, pc);
 }
 
 template <bool COUNT>
 __device__ __forceinline__ void finish_sample(Lane &S, const DevReq &R, float4 c, bool hit, PixCount &pc)
 {
-    S.acc.x += c.x;
-    S.acc.y += c.y;
-    S.acc.z += c.z;
-    S.acc.w += c.w;
+    acc4(S.acc, c);
     if (hit) {
         if (S.thit < S.dmin) {
             S.dmin = S.thit;
-            S.xbest = S.x;
+            if (R.saved) {
+                float *sv = reinterpret_cast<float *>(R.saved + pixel_index(R, S));
+                sv[0] = S.x.x;
+                sv[1] = S.x.y;
+                sv[2] = S.x.z;
+            }
         }
-        S.pflags |= S.sflags;
+        S.meta |= L_sflags(S) << 24;
     }
-    S.sample++;
+    L_set_sample(S, L_sample(S) + 1);
     begin_samples<COUNT>(S, R, pc);
 }
 
@@ -143,17 +179,17 @@ __device__ __forceinline__ void after_normal(Lane &S, const DevReq &R, PixCount 
 {
     if (R.shadows) {
         const float3 L = v3(R.light);
-        const float3 so = S.x + S.g * R.shadow_off;
+        const float3 so = offset_point(S.x, S.g, R.shadow_off);
         float s0, s1;
         bool sfp;
         if (COUNT) pc.v[kStatShadowRays] += 1;
         if (bounds(R, so, L, s0, s1, sfp)) {
-            S.phase = PH_SHADOW;
+            L_set_phase(S, PH_SHADOW);
+            S.cnt = 0;
             S.ro = so;
             S.rd = L;
             S.t = s0;
             S.t1 = s1;
-            S.steps = 0;
             begin_de(S, R, along(so, L, s0));
             return;
         }
@@ -165,13 +201,17 @@ __device__ __forceinline__ void after_normal(Lane &S, const DevReq &R, PixCount 
 template <bool COUNT>
 __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
 {
-    if (S.phase == PH_NORMAL) {
-        tap_accum(S.g, R.normal_mode, R.normal_h, S.tap, d);
+    const uint32_t phase = L_phase(S);
+    if (phase == PH_NORMAL) {
+        int tap = L_tap(S);
+        tap_accum(S.g, R.normal_mode, R.normal_h, tap, d);
         if (COUNT) pc.v[kStatNormalDE] += 1;
-        S.tap++;
+        tap++;
         const int taps = R.normal_mode == 0 ? 4 : 6;
-        if (S.tap < taps) {
-            begin_de(S, R, tap_point(S.x, R.normal_mode, R.normal_h, S.tap));
+        if (tap < taps) {
+            L_set_tap(S, tap);
+            S.ro = tap_point(S.x, R.normal_mode, R.normal_h, tap);
+            begin_de(S, R, S.ro);
             return;
         }
         S.g = finish_normal(S.g, S.rd);
@@ -179,23 +219,24 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
         return;
     }
     // one step of a camera or shadow march
-    S.steps++;
-    if (COUNT) pc.v[S.phase == PH_PRIMARY ? kStatPrimaryDE : kStatShadowDE] += 1;
+    const int steps = L_steps(S) + 1;
+    S.cnt = (uint32_t)steps << 11;
+    if (COUNT) pc.v[phase == PH_PRIMARY ? kStatPrimaryDE : kStatShadowDE] += 1;
     bool hit = d < R.eps;
     bool miss = false;
     if (!hit) {
-        S.t += (d < R.max_step) ? d : R.max_step;
+        S.t = march_step(S.t, d, R.max_step);
         if (S.t > S.t1)
             miss = true;
-        else if (S.steps >= R.max_steps)
+        else if (steps >= R.max_steps)
             hit = true;  // out of steps inside the interval: the listing reports a hit
     }
     if (!hit && !miss) {
         begin_de(S, R, along(S.ro, S.rd, S.t));
         return;
     }
-    if (S.phase == PH_SHADOW) {
-        if (hit) S.sflags |= kFlagShadow;
+    if (phase == PH_SHADOW) {
+        if (hit) L_set_sflags(S, L_sflags(S) | kFlagShadow);
         finish_sample<COUNT>(S, R, shade(R, S.g, hit ? 0.0f : 1.0f), true, pc);
         return;
     }
@@ -205,17 +246,18 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
     }
     S.thit = S.t;
     S.x = along(S.ro, S.rd, S.t);
-    S.sflags = kFlagHit;
-    if (S.fp && S.steps == 1) {  // first sample on the cut plane is inside: the cut face
+    L_set_sflags(S, kFlagHit);
+    if (L_fp(S) && steps == 1) {  // first sample on the cut plane is inside: the cut face
         S.g = v3(R.plane_hat);
-        S.sflags |= kFlagFace;
+        L_set_sflags(S, kFlagHit | kFlagFace);
         after_normal<COUNT>(S, R, pc);
         return;
     }
-    S.phase = PH_NORMAL;
-    S.tap = 0;
+    L_set_phase(S, PH_NORMAL);
+    L_set_tap(S, 0);
     S.g = v3(0.0f, 0.0f, 0.0f);
-    begin_de(S, R, tap_point(S.x, R.normal_mode, R.normal_h, 0));
+    S.ro = tap_point(S.x, R.normal_mode, R.normal_h, 0);
+    begin_de(S, R, S.ro);
 }
 
 // Queue unit u -> (request, pixel).  Units of a request are its 8 x 4 tiles
@@ -239,21 +281,17 @@ __device__ __forceinline__ void start_pixel(Lane &S, long long u, const DevReq *
     const int px = (int)(tile % R.tiles_x) * kTileW + (w & (kTileW - 1));
     const int py = (int)(tile / R.tiles_x) * kTileH + (w / kTileW);
     if (px >= R.width || py >= R.height) return;  // empty slot: the lane stays idle
-    S.req = lo;
-    S.px = px;
-    S.py = py;
-    S.sample = 0;
+    S.pix = (uint32_t)px | ((uint32_t)py << 16);
+    S.meta = (uint32_t)lo;  // phase idle, sample 0, flags 0
     S.acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     S.dmin = __int_as_float(0x7f800000);
-    S.xbest = v3(0.0f, 0.0f, 0.0f);
-    S.pflags = 0;
     if (COUNT)
 #pragma unroll
         for (int k = 0; k < kNStats; k++) pc.v[k] = 0;
     begin_samples<COUNT>(S, R, pc);
 }
 
-// resident 256-thread CTAs the register budget is fitted to (3 -> <= 85 registers, 24 warps per SM)
+// resident 256-thread CTAs the register budget is fitted to
 #ifndef FR_PERSIST_MIN_BLOCKS
 #define FR_PERSIST_MIN_BLOCKS 2
 #endif
@@ -279,65 +317,71 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
     const unsigned below = (1u << lane) - 1u;
     const unsigned long long total = (unsigned long long)A.total_units;
     Lane S;
-    S.phase = PH_IDLE;
-    S.req = 0;
+    S.meta = 0;  // idle
     PixCount pc;
 #pragma unroll
     for (int k = 0; k < kNStats; k++) pc.v[k] = 0;
+    // the warp's reservation [res, res_end) of queue units (warp-uniform)
+    unsigned long long res = 0, res_end = 0;
     bool exhausted = false;
 
     for (;;) {
         // ---- refill idle lanes (warp-uniform control flow)
-        unsigned idle = __ballot_sync(FULL, S.phase == PH_IDLE);
-        while (idle != 0u && !exhausted && (__popc(idle) >= A.refill_threshold || idle == FULL)) {
-            const int n = __popc(idle);
-            const int leader = __ffs(idle) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(A.queue, (unsigned long long)n);
-            base = __shfl_sync(FULL, base, leader);
-            if (base + (unsigned long long)n >= total) exhausted = true;
-            if (S.phase == PH_IDLE) {
-                const unsigned long long u = base + (unsigned long long)__popc(idle & below);
-                if (u < total) start_pixel<COUNT>(S, (long long)u, sreq, sbegin, nq, pc);
+        unsigned idle = __ballot_sync(FULL, L_phase(S) == PH_IDLE);
+        while (idle != 0u && (__popc(idle) >= A.refill_threshold || idle == FULL)) {
+            if (res >= res_end) {
+                if (exhausted) break;
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(A.queue, (unsigned long long)A.chunk);
+                base = __shfl_sync(FULL, base, 0);
+                if (base >= total) {
+                    exhausted = true;
+                    break;
+                }
+                res = base;
+                res_end = min(base + (unsigned long long)A.chunk, total);
             }
-            idle = __ballot_sync(FULL, S.phase == PH_IDLE);
+            const unsigned long long avail = res_end - res;
+            const unsigned rank = __popc(idle & below);
+            if (L_phase(S) == PH_IDLE && rank < avail)
+                start_pixel<COUNT>(S, (long long)(res + rank), sreq, sbegin, nq, pc);
+            res += min((unsigned long long)__popc(idle), avail);
+            idle = __ballot_sync(FULL, L_phase(S) == PH_IDLE);
         }
-        if (idle == FULL) {
-            if (exhausted) break;
-            continue;
-        }
+        if (idle == FULL && exhausted) break;
         // ---- a few orbit steps for every busy lane, then the ray's next move
-        if (S.phase != PH_IDLE) {
-            const DevReq &R = sreq[S.req];
-            bool done = false;
+        if (L_phase(S) != PH_IDLE) {
+            const DevReq &R = sreq[L_req(S)];
             if (R.kind == 0) {
                 const float4 c = R.c;
+                bool done = false;
                 if (R.power == 2) {
 #pragma unroll
                     for (int j = 0; j < KJ; j++)
                         if (!done) {
                             julia2_step(S.o, c);
-                            S.it++;
-                            done = (S.o.m > R.esc2) || (S.it >= R.max_iter);
+                            S.cnt++;
+                            done = (S.o.m > R.esc2) || (L_it(S) >= R.max_iter);
                         }
                 } else {
 #pragma unroll
                     for (int j = 0; j < KJ; j++)
                         if (!done) {
                             julia3_step(S.o, c);
-                            S.it++;
-                            done = (S.o.m > R.esc2) || (S.it >= R.max_iter);
+                            S.cnt++;
+                            done = (S.o.m > R.esc2) || (L_it(S) >= R.max_iter);
                         }
                 }
                 if (done) {
-                    if (COUNT) pc.v[kStatOrbit] += S.it;
+                    if (COUNT) pc.v[kStatOrbit] += L_it(S);
                     advance<COUNT>(S, R, julia_dist(S.o), pc);
                 }
             } else {
-                bulb_step(S.o, S.cpt, R.power);
-                S.it++;
-                if ((S.o.m > R.esc2) || (S.it >= R.max_iter)) {
-                    if (COUNT) pc.v[kStatOrbit] += S.it;
+                const float3 cpt = (L_phase(S) == PH_NORMAL) ? S.ro : along(S.ro, S.rd, S.t);
+                bulb_step(S.o, cpt, R.power);
+                S.cnt++;
+                if ((S.o.m > R.esc2) || (L_it(S) >= R.max_iter)) {
+                    if (COUNT) pc.v[kStatOrbit] += L_it(S);
                     advance<COUNT>(S, R, bulb_dist(S.o), pc);
                 }
             }
@@ -363,10 +407,13 @@ static cudaError_t launch_persist_t(const BatchArgs &A, int block, int ctas_per_
     return cudaGetLastError();
 }
 
+static_assert(sizeof(BatchArgs) <= 32764, "the request table must fit the kernel parameter space");
+
 cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int unroll, bool count,
                            cudaStream_t s)
 {
-    if (count) return launch_persist_t<2, true>(A, block, ctas_per_sm, s);
+    if (count) return launch_persist_t<4, true>(A, block, ctas_per_sm, s);
+    if (unroll == 8) return launch_persist_t<8, false>(A, block, ctas_per_sm, s);
     if (unroll == 4) return launch_persist_t<4, false>(A, block, ctas_per_sm, s);
     if (unroll == 2) return launch_persist_t<2, false>(A, block, ctas_per_sm, s);
     return launch_persist_t<1, false>(A, block, ctas_per_sm, s);

@@ -23,7 +23,7 @@ __device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, flo
         steps++;
         if (COUNT) cnt.v[kStatOrbit] += trips;
         if (d < R.eps) break;
-        t += (d < R.max_step) ? d : R.max_step;
+        t = march_step(t, d, R.max_step);
         if (t > t1) {
             hit = false;
             break;
@@ -79,7 +79,7 @@ __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float
     float vis = 1.0f;
     if (R.shadows) {
         float3 L = v3(R.light);
-        float3 so = x + n * R.shadow_off;
+        float3 so = offset_point(x, n, R.shadow_off);
         float s0, s1, ts;
         bool sfp;
         int ss;
@@ -112,19 +112,14 @@ __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Co
         camera_ray(R, px, py, s, ro, rd);
         if (COUNT) cnt.v[kStatPrimaryRays] += 1;
         float4 c = trace_sample<KIND, U, COUNT>(R, ro, rd, t, f, x, cnt);
-        acc.x += c.x;
-        acc.y += c.y;
-        acc.z += c.z;
-        acc.w += c.w;
+        acc4(acc, c);
         if ((f & kFlagHit) && t < dmin) {
             dmin = t;
             xh = x;
         }
         fl |= f;
     }
-    const float fs = (float)R.spp;
-    acc = make_float4(acc.x / fs, acc.y / fs, acc.z / fs, acc.w / fs);
-    store_pixel(R, px, py, acc, dmin, xh, fl);
+    store_pixel(R, px, py, mean4(acc, R.spp), dmin, xh, fl);
 }
 
 }  // namespace fr
