@@ -147,8 +147,7 @@ def test_null_structs_refused(F):
 
 def test_tuning_roundtrip_and_checks(F):
     t = F.fr_get_tuning()
-    old = (t.plain_block, t.plain_unroll, t.persist_block, t.persist_ctas_per_sm,
-           t.refill_threshold, t.persist_unroll)
+    old = tuple(getattr(t, n) for n, _ in F.fr_tuning._fields_)
     bad = F.fr_tuning(*old)
     bad.plain_block = 48
     assert F.fr_set_tuning(bad) == F.FR_EINVAL
@@ -157,6 +156,9 @@ def test_tuning_roundtrip_and_checks(F):
     assert F.fr_set_tuning(bad) == F.FR_EINVAL
     bad = F.fr_tuning(*old)
     bad.refill_threshold = 0
+    assert F.fr_set_tuning(bad) == F.FR_EINVAL
+    bad = F.fr_tuning(*old)
+    bad.queue_chunk = 48
     assert F.fr_set_tuning(bad) == F.FR_EINVAL
     good = F.fr_tuning(*old)
     good.plain_block = 64
