@@ -61,6 +61,12 @@ def workload(name: str, rank: int = 0):
         return [W.stress_bulb_4k(60 + rank)], "Mandelbulb n=8 3840x2160 4 spp, iteration cap 12 (frame 60)"
     if name == "stress_julia_4k":
         return [W.stress_julia_4k()], "quaternion Julia 3840x2160 with shadow rays"
+    if name == "diff_julia":
+        s, start = W.diff_julia(W.BASE_SEED + rank)
+        return [s], "differentiable Julia 512x512: forward with saved state + implicit-diff adjoint"
+    if name == "stress_anim":
+        return [W.stress_bulb_4k(k) for k in range(0, 120, 40)], (
+            "Mandelbulb n=8 3840x2160 4 spp, 120 frames, iteration cap 4..20")
     raise SystemExit("unknown workload " + name)
 
 
@@ -244,12 +250,17 @@ def time_steps(torch, step, steps, stream, flush, dist=None, clk_index=None):
     if dist:
         dist.barrier()
     times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total = sum(times) / 1e3
-    if dist:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(torch, dist, sum(times) / 1e3, "cuda")
     return times, total, (clk.summary() if clk else None)
+
+
+def max_over_ranks(torch, dist, seconds: float, device) -> float:
+    """The job's time is its slowest rank's (weak scaling: no exchange on the data path)."""
+    if not dist:
+        return seconds
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def count_frame(api, torch, scenes):
@@ -267,6 +278,97 @@ def flops_of(scenes, per_scene_iters):
     return sum(flops_per_iter(s) * it for s, it in zip(scenes, per_scene_iters))
 
 
+def run_gradient(args, torch, api, F, scenes, desc, rank, world):
+    """One step = a differentiable Julia render (colour, depth, saved hit state) plus
+    the adjoint (fr_render_backward) of an L2 loss: gradients per second.  The
+    finite-difference alternative needs 22 forward renders per gradient (central
+    differences over c[4], plane n[3], offset, light[3])."""
+    s = scenes[0]
+    H, Wd = s["camera"]["height"], s["camera"]["width"]
+    out = api.alloc_image(s, rgba8=False, rgba=True, depth=True, saved=True)
+    target = api.render(s, rgba8=False, rgba=True, depth=False)["rgba"].clone()
+    grad = torch.zeros(11, dtype=torch.float32, device="cuda")
+    d_rgba = torch.empty_like(out["rgba"])
+    prm, pl, cam, li = api.julia_params(s), api.plane_struct(s), api.camera_struct(s), api.light_struct(s)
+    img = api.image_struct(out)
+    stream = api.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def forward():
+        F.check(F.fr_render_julia(prm, pl, cam, li, img, stream))
+
+    def step():
+        forward()
+        torch.sub(out["rgba"], target, out=d_rgba)  # dL/drgba of 0.5 |rgba - target|^2
+        F.check(F.fr_render_backward(prm, pl, cam, li, out["saved"].data_ptr(), d_rgba.data_ptr(),
+                                     None, grad.data_ptr(), stream))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    tstream = torch.cuda.current_stream()
+    times, total_s, clk = time_steps(torch, step, args.steps, tstream, flush, None, clk_index=0)
+    ftimes, ftotal, _ = time_steps(torch, forward, args.steps, tstream, flush, None)
+    grad_per_s = args.steps / total_s
+    fd_per_s = 1.0 / (22 * ftotal / args.steps)
+    e2e_t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+        grad.cpu()
+    e2e = args.steps / (time.perf_counter() - e2e_t0)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": "grad/s", "value": grad_per_s, "unit": "grad/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": desc, "width": Wd, "height": H,
+                                        "l2": "flushed between timed steps (256 MB write)"},
+        "forward_ms": ftotal / args.steps * 1e3,
+        "fd_grad_per_s": fd_per_s, "speedup_vs_fd": grad_per_s / fd_per_s,
+        "e2e": {"value": e2e, "unit": "grad/s", "h2d_bytes_per_step": ctypes_sizeof_inputs(F, 1),
+                "d2h_bytes_per_step": 44},
+        "gpu_launches": 2 * args.steps, "clocks": clk,
+    }))
+
+
+def run_animation(args, torch, api, F, desc, rank, world):
+    """The animated stress scene: 120 frames of the Mandelbulb at 3840x2160 with 4
+    jittered samples, iteration cap 4 + floor(16k/119) and the camera at azimuth
+    3k degrees; per-frame device time (CUDA events), median and p95."""
+    frames = [W.stress_bulb_4k(k) for k in range(120)]
+    out = api.alloc_image(frames[0], rgba8=True, depth=True)
+    ws = api.workspace(1)
+    stream = api.current_stream()
+    tstream = torch.cuda.current_stream()
+    arrs = [api.request_array([f], [out]) for f in frames]
+    for a in arrs[:args.warmup]:
+        F.check(F.fr_render_batch(a, 1, ws.data_ptr(), ws.numel(), stream))
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]
+    with ClockSampler(0) as clk:
+        for (a, b), arr in zip(ev, arrs):
+            a.record(tstream)
+            F.check(F.fr_render_batch(arr, 1, ws.data_ptr(), ws.numel(), stream))
+            b.record(tstream)
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    srt = sorted(ms)
+    rays = [3840 * 2160 * 4] * len(frames)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": "ms/frame", "value": statistics.median(ms), "unit": "ms", "n_gpus": world,
+        "steps": len(frames), "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": desc, "path": "persistent"},
+        "p95_ms": srt[int(0.95 * (len(srt) - 1))], "max_ms": srt[-1],
+        "per_frame_ms": [round(v, 3) for v in ms],
+        "primary_mrays_per_s": sum(rays) / (sum(ms) / 1e3) / 1e6,
+        "gpu_launches": len(frames), "clocks": clk.summary(),
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,6 +379,7 @@ def main():
     ap.add_argument("--path", default="persistent", choices=["plain", "persistent"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the current launch shape")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -306,6 +409,17 @@ def main():
     F.load()
     stream = api.current_stream(dev)
     tstream = torch.cuda.current_stream(dev)
+    if args.workload == "diff_julia":
+        return run_gradient(args, torch, api, F, scenes, desc, rank, world)
+    if args.workload == "stress_anim":
+        return run_animation(args, torch, api, F, desc, rank, world)
+
+    tuning = None
+    if args.path == "persistent" and not args.no_autotune:
+        from paper_2102_01747_gb300 import autotune
+
+        tuning = autotune.tune(scenes, reps=3)  # untimed search over the launch shape
+        tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"])}
 
     counts = count_frame(api, torch, scenes)
     per_scene_iters = []
@@ -394,6 +508,7 @@ def main():
                 "note": "inputs are the scene parameter structs passed in each call"},
         "gpu_launches": main_r["launches"] * args.steps,
         "clocks": c,
+        "tuning": tuning,
     }
     for path, r in results.items():
         if path != args.path:

@@ -133,6 +133,9 @@ typedef struct {
     float max_step;
     int32_t normal_mode;
     float normal_h;
+    int32_t algebraic;       /* 0: the listing's acos/atan2/sin/cos power; 1: the same
+                                Eq. 1 by de Moivre powers of cos + i sin, no
+                                transcendental calls in the orbit loop           */
 } fr_bulb_params;
 
 /* Output buffers (device).  Any may be NULL except that at least one of rgba8,
@@ -167,7 +170,6 @@ typedef struct {
     int32_t persist_ctas_per_sm; /* resident CTAs per SM; 0 = as many as fit            */
     int32_t refill_threshold;    /* refill a warp once this many lanes are idle (1..32) */
     int32_t persist_unroll;      /* Julia orbit steps per scheduling round: 1, 2, 4, 8  */
-    int32_t queue_chunk;         /* pixels a warp reserves per queue atomic (32..4096, x32) */
 } fr_tuning;
 
 /* Render one quaternion Julia image with the one-ray-per-thread kernel

@@ -47,7 +47,8 @@ class fr_julia_params(ctypes.Structure):
 class fr_bulb_params(ctypes.Structure):
     _fields_ = [("n", c_int32), ("max_iter", c_int32), ("bailout", c_float),
                 ("bound_radius", c_float), ("max_steps", c_int32), ("eps", c_float),
-                ("max_step", c_float), ("normal_mode", c_int32), ("normal_h", c_float)]
+                ("max_step", c_float), ("normal_mode", c_int32), ("normal_h", c_float),
+                ("algebraic", c_int32)]
 
 
 class fr_image(ctypes.Structure):
@@ -63,7 +64,7 @@ class fr_request(ctypes.Structure):
 class fr_tuning(ctypes.Structure):
     _fields_ = [("plain_block", c_int32), ("plain_unroll", c_int32), ("persist_block", c_int32),
                 ("persist_ctas_per_sm", c_int32), ("refill_threshold", c_int32),
-                ("persist_unroll", c_int32), ("queue_chunk", c_int32)]
+                ("persist_unroll", c_int32)]
 
 
 # every entry point of include/fr.h with its ctypes signature

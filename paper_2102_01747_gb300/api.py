@@ -43,6 +43,7 @@ def bulb_params(scene: dict) -> F.fr_bulb_params:
     p.max_step = float(scene["max_step"])
     p.normal_mode = F.FR_NORMAL_TETRA if scene["normal_mode"] == "tetra" else F.FR_NORMAL_CENTRAL
     p.normal_h = float(scene["normal_h"])
+    p.algebraic = 1 if scene.get("algebraic") else 0
     return p
 
 

@@ -1,0 +1,126 @@
+"""Autotuner for the persistent kernel's launch shape (fr_tuning).
+
+The knobs are the ones the batched path is sensitive to:
+  persist_block      threads per CTA (64, 128, 256)
+  refill_threshold   idle lanes that trigger a warp refill (the compaction interval)
+  persist_unroll     Julia orbit steps per scheduling round (the unroll depth)
+The search is coordinate descent from the current setting: each knob in turn is
+swept with the others fixed, each candidate timed with CUDA events (median of a
+few launches of fr_render_batch on the caller's scenes), and the best kept.
+Results are cached in a JSON file keyed by GPU name and workload key, so a
+later process applies them without searching again.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import _ffi as F
+from . import api
+
+SPACE = {
+    "persist_block": (64, 128, 256),
+    "refill_threshold": (1, 2, 4, 8, 16),
+    "persist_unroll": (2, 4, 8),
+}
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
+
+
+def current() -> dict:
+    t = F.fr_get_tuning()
+    return {n: getattr(t, n) for n, _ in F.fr_tuning._fields_}
+
+
+def apply(cfg: dict) -> None:
+    t = F.fr_get_tuning()
+    for k, v in cfg.items():
+        setattr(t, k, int(v))
+    F.check(F.fr_set_tuning(t))
+
+
+def _time_batch(scenes, outs, ws, reps: int) -> float:
+    arr = api.request_array(scenes, outs)
+    stream = api.current_stream()
+    run = lambda: F.check(F.fr_render_batch(arr, len(scenes), ws.data_ptr(), ws.numel(), stream))  # noqa: E731
+    run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=None) -> dict:
+    """Coordinate descent over `space`; returns {"config": ..., "ms": ..., "trials": [...]}
+    and leaves the best configuration applied."""
+    space = space or SPACE
+    outs = [api.alloc_image(s) for s in scenes]
+    ws = api.workspace(len(scenes))
+    best = current()
+    best_ms = _time_batch(scenes, outs, ws, reps)
+    trials = [dict(best, ms=best_ms)]
+    for _ in range(passes):
+        for knob, values in space.items():
+            for v in values:
+                if v == best[knob]:
+                    continue
+                cand = dict(best, **{knob: v})
+                apply(cand)
+                ms = _time_batch(scenes, outs, ws, reps)
+                trials.append(dict(cand, ms=ms))
+                if log:
+                    log("%s=%s: %.3f ms" % (knob, v, ms))
+                if ms < best_ms:
+                    best, best_ms = cand, ms
+            apply(best)
+    apply(best)
+    return {"config": best, "ms": best_ms, "trials": trials}
+
+
+def gpu_key() -> str:
+    return torch.cuda.get_device_name()
+
+
+def load_cached(key: str, path: str = DEFAULT_CACHE):
+    if not os.path.exists(path):
+        return None
+    try:
+        return json.load(open(path)).get(gpu_key(), {}).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def save_cached(key: str, cfg: dict, ms: float, path: str = DEFAULT_CACHE) -> None:
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    data = {}
+    if os.path.exists(path):
+        try:
+            data = json.load(open(path))
+        except (OSError, ValueError):
+            data = {}
+    data.setdefault(gpu_key(), {})[key] = {"config": cfg, "ms": ms}
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1)
+    os.replace(tmp, path)
+
+
+def tuned(key: str, scenes, reps: int = 5, path: str = DEFAULT_CACHE, retune: bool = False) -> dict:
+    """Apply the cached configuration for `key`, or search for it (and cache it)."""
+    hit = None if retune else load_cached(key, path)
+    if hit:
+        apply(hit["config"])
+        return {"config": hit["config"], "ms": hit["ms"], "cached": True}
+    res = tune(scenes, reps=reps)
+    save_cached(key, res["config"], res["ms"], path)
+    res["cached"] = False
+    return res

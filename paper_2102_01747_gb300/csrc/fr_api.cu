@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 128, 0, 4, 4, 64};
+fr_tuning g_tuning = {128, 1, 64, 0, 16, 4};
 
 fr_tuning tuning()
 {
@@ -118,6 +118,8 @@ fr_status resolve_bulb(fr::DevReq &R, const fr_bulb_params *P)
     R.power = P->n;
     R.slice_w = 0.0f;
     R.esc2 = P->bailout * P->bailout;
+    if (P->algebraic != 0 && P->algebraic != 1) return fail(FR_EINVAL, "algebraic must be 0 or 1");
+    R.bulb_alg = P->algebraic;
     return resolve_march(R, P->max_iter, P->bound_radius, P->max_steps, P->eps, P->max_step,
                          P->normal_mode, P->normal_h);
 }
@@ -230,8 +232,6 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
         return fail(FR_EINVAL, "block sizes must be multiples of 32 in 32..256");
     if (!unroll_ok(t->plain_unroll) || !(unroll_ok(t->persist_unroll) || t->persist_unroll == 8))
         return fail(FR_EINVAL, "unroll depth must be 1, 2 or 4 (persistent: also 8)");
-    if (t->queue_chunk < 32 || t->queue_chunk > 4096 || t->queue_chunk % 32)
-        return fail(FR_EINVAL, "queue_chunk must be a multiple of 32 in 32..4096");
     if (t->persist_ctas_per_sm < 0 || t->persist_ctas_per_sm > 32)
         return fail(FR_EINVAL, "persist_ctas_per_sm outside 0..32");
     if (t->refill_threshold < 1 || t->refill_threshold > 32)
@@ -319,7 +319,6 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         A.n_reqs = n;
         A.total_units = units;
         A.refill_threshold = tu.refill_threshold;
-        A.chunk = tu.queue_chunk;
         A.queue = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 256 * (size_t)chunk);
         const fr_status st = launched(fr::launch_persist(A, tu.persist_block, tu.persist_ctas_per_sm,
                                                          tu.persist_unroll, count, (cudaStream_t)stream));

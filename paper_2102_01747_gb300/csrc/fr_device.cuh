@@ -50,7 +50,7 @@ struct __align__(16) DevReq {
     int plane_on;
     int shadows;
     int spp;
-    int pad0;
+    int bulb_alg;         // Mandelbulb power without transcendental calls
     float4 plane;         // n.xyz, offset
     float4 plane_hat;     // n / |n|
     float4 eye;
@@ -287,6 +287,63 @@ __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
     o.m = dot3(v3(o.a, o.b, o.c), v3(o.a, o.b, o.c));
 }
 
+// (c + i s)^k for an integer k >= 1 by binary exponentiation of complex numbers
+__device__ __forceinline__ void cpow_int(float c, float s, int k, float &rc, float &rs)
+{
+    float ac = 1.0f, as = 0.0f, bc = c, bs = s;
+    while (k > 0) {
+        if (k & 1) {
+            const float t = fmaf(ac, bc, -mul(as, bs));
+            as = fmaf(ac, bs, mul(as, bc));
+            ac = t;
+        }
+        k >>= 1;
+        if (k) {
+            const float t = fmaf(bc, bc, -mul(bs, bs));
+            bs = mul(2.0f, mul(bc, bs));
+            bc = t;
+        }
+    }
+    rc = ac;
+    rs = as;
+}
+
+// The same step with Eq. 1 evaluated without transcendental calls: with
+// r = |w| and rho = |(w.x, w.z)|, the angles of the listing have
+// cos b0 = w.y / r, sin b0 = rho / r (b0 in [0, pi]) and cos a0 = w.z / rho,
+// sin a0 = w.x / rho, so (cos n b0, sin n b0) and (cos n a0, sin n a0) are the
+// n-th powers of the unit complex numbers cos + i sin (de Moivre).  On the
+// polar axis (rho = 0) a0 is taken as 0.
+__device__ __forceinline__ void bulb_step_alg(Orbit &o, float3 cpt, int n)
+{
+    const float nf = (float)n;
+    const float r = sqrtf(o.m);
+    const float rn1 = ipow(r, n - 1);
+    o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
+    float px = 0.0f, py = 0.0f, pz = 0.0f;
+    if (r > 0.0f) {
+        const float rho = sqrtf(fmaf(o.c, o.c, mul(o.a, o.a)));
+        const float cb0 = fminf(fmaxf(dvd(o.b, r), -1.0f), 1.0f);
+        const float sb0 = dvd(rho, r);
+        float ca0 = 1.0f, sa0 = 0.0f;
+        if (rho > 0.0f) {
+            ca0 = dvd(o.c, rho);
+            sa0 = dvd(o.a, rho);
+        }
+        float cb, sb, ca, sa;
+        cpow_int(cb0, sb0, n, cb, sb);
+        cpow_int(ca0, sa0, n, ca, sa);
+        const float rn = mul(rn1, r);
+        px = mul(rn, mul(sb, sa));
+        py = mul(rn, cb);
+        pz = mul(rn, mul(sb, ca));
+    }
+    o.a = add(px, cpt.x);
+    o.b = add(py, cpt.y);
+    o.c = add(pz, cpt.z);
+    o.m = dot3(v3(o.a, o.b, o.c), v3(o.a, o.b, o.c));
+}
+
 __device__ __forceinline__ float bulb_dist(const Orbit &o)
 {
     return dvd(mul(mul(0.25f, logf(o.m)), sqrtf(o.m)), o.dz);
@@ -328,14 +385,17 @@ __device__ __forceinline__ float julia_de3(const float4 c, float slice_w, int ma
 }
 
 template <int U>
-__device__ __forceinline__ float bulb_de(int n, int max_iter, float esc2, float3 c, int &trips)
+__device__ __forceinline__ float bulb_de(int n, int max_iter, float esc2, float3 c, int alg, int &trips)
 {
     Orbit o;
     bulb_init(o, c);
     int i = 0;
 #pragma unroll U
     for (int k = 0; k < max_iter; k++) {
-        bulb_step(o, c, n);
+        if (alg)
+            bulb_step_alg(o, c, n);
+        else
+            bulb_step(o, c, n);
         i++;
         if (o.m > esc2) break;
     }
@@ -350,7 +410,7 @@ __device__ __forceinline__ float de(const DevReq &R, float3 p, int &trips)
         if (R.power == 2) return julia_de2<U>(R.c, R.slice_w, R.max_iter, R.esc2, p, trips);
         return julia_de3<U>(R.c, R.slice_w, R.max_iter, R.esc2, p, trips);
     }
-    return bulb_de<U>(R.power, R.max_iter, R.esc2, p, trips);
+    return bulb_de<U>(R.power, R.max_iter, R.esc2, p, R.bulb_alg, trips);
 }
 
 // ------------------------------------------------------------------ normal stencils

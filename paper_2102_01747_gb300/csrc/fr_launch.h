@@ -16,8 +16,6 @@ struct BatchArgs {
     long long total_units;      // pixel slots over all requests
     int n_reqs;
     int refill_threshold;       // refill a warp once this many lanes are idle
-    int chunk;                  // pixels a warp reserves per atomic on the queue head
-    int pad;
     DevReq reqs[kMaxReqPerLaunch];
 };
 

@@ -17,10 +17,10 @@
 // tap or shadow step, Listing "Julia Set ray cast") and starts its next orbit
 // at once, so lanes never wait for each other's orbits or rays.  A finished
 // pixel is stored and its lane refilled from one queue over every pixel of
-// every request.  Each warp reserves `chunk` pixels at a time with a single
-// atomicAdd on the queue head and hands them to its idle lanes by ballot rank
-// once `refill_threshold` lanes are idle; the reservation keeps the atomics
-// on the one queue head rare (they serialise in L2).
+// every request: once `refill_threshold` lanes are idle the warp takes exactly
+// that many pixels with one atomicAdd on the queue head and hands them out by
+// ballot rank.  (Reserving more than the idle lanes, to make the atomics rarer,
+// measured slower: pixels parked in a busy warp starve the others at the end.)
 //
 // The orbit steps, the distance, the march update and the stencils are the
 // same device functions, with every rounding step spelled out, that the
@@ -275,11 +275,12 @@ __device__ __forceinline__ void start_pixel(Lane &S, long long u, const DevReq *
             hi = mid - 1;
     }
     const DevReq &R = sreq[lo];
-    const long long local = u - sbegin[lo];
-    const long long tile = local >> 5;
-    const int w = (int)(local & 31);
-    const int px = (int)(tile % R.tiles_x) * kTileW + (w & (kTileW - 1));
-    const int py = (int)(tile / R.tiles_x) * kTileH + (w / kTileW);
+    const int local = (int)(u - sbegin[lo]);  // < 2^31: a request has fewer pixels slots
+    const int tile = local >> 5;
+    const int w = local & 31;
+    const int ty = tile / R.tiles_x;
+    const int px = (tile - ty * R.tiles_x) * kTileW + (w & (kTileW - 1));
+    const int py = ty * kTileH + (w / kTileW);
     if (px >= R.width || py >= R.height) return;  // empty slot: the lane stays idle
     S.pix = (uint32_t)px | ((uint32_t)py << 16);
     S.meta = (uint32_t)lo;  // phase idle, sample 0, flags 0
@@ -321,31 +322,22 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
     PixCount pc;
 #pragma unroll
     for (int k = 0; k < kNStats; k++) pc.v[k] = 0;
-    // the warp's reservation [res, res_end) of queue units (warp-uniform)
-    unsigned long long res = 0, res_end = 0;
     bool exhausted = false;
 
     for (;;) {
-        // ---- refill idle lanes (warp-uniform control flow)
+        // ---- refill idle lanes (warp-uniform control flow): one atomicAdd takes
+        // exactly as many queue units as the warp has idle lanes
         unsigned idle = __ballot_sync(FULL, L_phase(S) == PH_IDLE);
-        while (idle != 0u && (__popc(idle) >= A.refill_threshold || idle == FULL)) {
-            if (res >= res_end) {
-                if (exhausted) break;
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(A.queue, (unsigned long long)A.chunk);
-                base = __shfl_sync(FULL, base, 0);
-                if (base >= total) {
-                    exhausted = true;
-                    break;
-                }
-                res = base;
-                res_end = min(base + (unsigned long long)A.chunk, total);
+        while (idle != 0u && !exhausted && (__popc(idle) >= A.refill_threshold || idle == FULL)) {
+            const int n = __popc(idle);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(A.queue, (unsigned long long)n);
+            base = __shfl_sync(FULL, base, 0);
+            if (base + (unsigned long long)n >= total) exhausted = true;
+            if (L_phase(S) == PH_IDLE) {
+                const unsigned long long u = base + (unsigned long long)__popc(idle & below);
+                if (u < total) start_pixel<COUNT>(S, (long long)u, sreq, sbegin, nq, pc);
             }
-            const unsigned long long avail = res_end - res;
-            const unsigned rank = __popc(idle & below);
-            if (L_phase(S) == PH_IDLE && rank < avail)
-                start_pixel<COUNT>(S, (long long)(res + rank), sreq, sbegin, nq, pc);
-            res += min((unsigned long long)__popc(idle), avail);
             idle = __ballot_sync(FULL, L_phase(S) == PH_IDLE);
         }
         if (idle == FULL && exhausted) break;
@@ -378,7 +370,10 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
                 }
             } else {
                 const float3 cpt = (L_phase(S) == PH_NORMAL) ? S.ro : along(S.ro, S.rd, S.t);
-                bulb_step(S.o, cpt, R.power);
+                if (R.bulb_alg)
+                    bulb_step_alg(S.o, cpt, R.power);
+                else
+                    bulb_step(S.o, cpt, R.power);
                 S.cnt++;
                 if ((S.o.m > R.esc2) || (L_it(S) >= R.max_iter)) {
                     if (COUNT) pc.v[kStatOrbit] += L_it(S);

@@ -157,9 +157,6 @@ def test_tuning_roundtrip_and_checks(F):
     bad = F.fr_tuning(*old)
     bad.refill_threshold = 0
     assert F.fr_set_tuning(bad) == F.FR_EINVAL
-    bad = F.fr_tuning(*old)
-    bad.queue_chunk = 48
-    assert F.fr_set_tuning(bad) == F.FR_EINVAL
     good = F.fr_tuning(*old)
     good.plain_block = 64
     assert F.fr_set_tuning(good) == F.FR_OK
