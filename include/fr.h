@@ -201,6 +201,22 @@ FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs);
 FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *workspace,
                                  size_t ws_bytes, void *stream);
 
+/* fr_render_batch without a caller-provided workspace.  The paper has no
+ * counterpart: this is for callers that cannot allocate device memory -- a
+ * plugin whose host application owns every device allocation, or a frame loop
+ * that may not call cudaMalloc once running (it can synchronise the device and
+ * break frame pacing).  The queue heads live in a 16 KB file-scope __device__
+ * array of the library, enough for the largest batch fr_render_batch accepts
+ * (4096 requests); every GPU that loads the library keeps it until exit.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * with that device current, so make that first call before any stream
+ * capture.  Nothing is allocated: no cudaMalloc, cudaFree or allocating
+ * library call.  The array is shared by every call (each launch zeroes its own
+ * queue head first), so calls that overlap on the GPU -- on different streams,
+ * or from different threads -- race on it; serialise them.  Errors: as
+ * fr_render_batch, plus FR_EINVAL for n_reqs outside 1..4096. */
+FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, void *stream);
+
 /* Vector-Jacobian product of a Julia render (spp = 1) by implicit
  * differentiation at the hit point: for surface hits
  *     dt/dtheta = -(dd/dtheta) / (grad_x d . rd),

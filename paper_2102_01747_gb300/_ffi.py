@@ -78,6 +78,7 @@ SIGNATURES = {
     "fr_batch_workspace_bytes": (ctypes.c_size_t, [c_int32]),
     "fr_render_batch": (c_int32, [ctypes.POINTER(fr_request), c_int32, c_void_p, ctypes.c_size_t,
                                   c_void_p]),
+    "fr_render_batch_static": (c_int32, [ctypes.POINTER(fr_request), c_int32, c_void_p]),
     "fr_render_backward": (c_int32, [ctypes.POINTER(fr_julia_params), ctypes.POINTER(fr_plane),
                                      ctypes.POINTER(fr_camera), ctypes.POINTER(fr_light), c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -144,6 +145,10 @@ def fr_batch_workspace_bytes(n_reqs):
 
 def fr_render_batch(reqs, n_reqs, workspace, ws_bytes, stream=None):
     return load().fr_render_batch(reqs, int(n_reqs), workspace, int(ws_bytes), stream)
+
+
+def fr_render_batch_static(reqs, n_reqs, stream=None):
+    return load().fr_render_batch_static(reqs, int(n_reqs), stream)
 
 
 def fr_render_backward(params, plane, camera, light, saved, d_rgba, d_depth, grad, stream=None):

@@ -210,6 +210,11 @@ fr_status launched(cudaError_t e)
 
 }  // namespace
 
+namespace fr {
+// error reporting for entry points defined in other translation units
+fr_status set_error(fr_status st, const char *msg) { return fail(st, "%s", msg); }
+}  // namespace fr
+
 extern "C" {
 
 FR_API int32_t fr_abi_version(void) { return 1; }
