@@ -376,7 +376,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bulb_1080p")
-    ap.add_argument("--path", default="persistent", choices=["plain", "persistent"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "persistent"],
+                    help="auto: one-ray-per-thread kernel for one request, persistent for batches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the current launch shape")
@@ -409,6 +410,8 @@ def main():
     F.load()
     stream = api.current_stream(dev)
     tstream = torch.cuda.current_stream(dev)
+    if args.path == "auto":
+        args.path = "plain" if len(scenes) == 1 else "persistent"
     if args.workload == "diff_julia":
         return run_gradient(args, torch, api, F, scenes, desc, rank, world)
     if args.workload == "stress_anim":

