@@ -17,13 +17,10 @@
 // tap or shadow step, Listing "Julia Set ray cast") and starts its next orbit
 // at once, so lanes never wait for each other's orbits or rays.  A finished
 // pixel is stored and its lane refilled from one queue over every pixel of
-// every request: once `refill_threshold` lanes are idle the warp hands them
-// that many pixels by ballot rank.  The pixels come from one atomicAdd on the
-// queue head issued at the previous refill, so the atomic's round trip (long
-// under contention from every warp of the GPU) overlaps the orbit work.  Only
-// that one refill's worth is reserved ahead: reserving more, to make the
-// atomics rarer, measured slower (pixels parked in a busy warp starve the
-// others at the end of the queue).
+// every request: once `refill_threshold` lanes are idle the warp takes exactly
+// that many pixels with one atomicAdd on the queue head and hands them out by
+// ballot rank.  (Reserving more than the idle lanes, to make the atomics rarer,
+// measured slower: pixels parked in a busy warp starve the others at the end.)
 //
 // The orbit steps, the distance, the march update and the stencils are the
 // same device functions, with every rounding step spelled out, that the
@@ -326,39 +323,22 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
 #pragma unroll
     for (int k = 0; k < kNStats; k++) pc.v[k] = 0;
     bool exhausted = false;
-    // one queue reservation of `thr` units is kept in flight: lane 0 issues the
-    // atomicAdd right after a refill and the warp reads the result at its next
-    // refill, so the atomic's round trip overlaps the orbit work
-    const int thr = A.refill_threshold;
-    bool have_pre = false;          // warp-uniform
-    unsigned long long pre0 = 0;    // the reservation's first unit (lane 0's register)
 
     for (;;) {
-        // ---- refill idle lanes (warp-uniform control flow)
+        // ---- refill idle lanes (warp-uniform control flow): one atomicAdd takes
+        // exactly as many queue units as the warp has idle lanes
         unsigned idle = __ballot_sync(FULL, L_phase(S) == PH_IDLE);
-        while (idle != 0u && !exhausted && (__popc(idle) >= thr || idle == FULL)) {
-            int n = __popc(idle);
-            unsigned long long base;
-            if (have_pre) {
-                base = __shfl_sync(FULL, pre0, 0);
-                have_pre = false;
-                n = min(n, thr);
-            } else {
-                unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(A.queue, (unsigned long long)n);
-                base = __shfl_sync(FULL, b, 0);
-            }
+        while (idle != 0u && !exhausted && (__popc(idle) >= A.refill_threshold || idle == FULL)) {
+            const int n = __popc(idle);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(A.queue, (unsigned long long)n);
+            base = __shfl_sync(FULL, base, 0);
             if (base + (unsigned long long)n >= total) exhausted = true;
             if (L_phase(S) == PH_IDLE) {
-                const unsigned rank = __popc(idle & below);
-                const unsigned long long u = base + rank;
-                if ((int)rank < n && u < total) start_pixel<COUNT>(S, (long long)u, sreq, sbegin, nq, pc);
+                const unsigned long long u = base + (unsigned long long)__popc(idle & below);
+                if (u < total) start_pixel<COUNT>(S, (long long)u, sreq, sbegin, nq, pc);
             }
             idle = __ballot_sync(FULL, L_phase(S) == PH_IDLE);
-        }
-        if (!have_pre && !exhausted) {
-            if (lane == 0) pre0 = atomicAdd(A.queue, (unsigned long long)thr);
-            have_pre = true;
         }
         if (idle == FULL && exhausted) break;
         // ---- a few orbit steps for every busy lane, then the ray's next move

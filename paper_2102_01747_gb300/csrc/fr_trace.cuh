@@ -7,27 +7,6 @@
 
 namespace fr {
 
-// The Mandelbulb DE with its math-library calls is long; inlined at the three
-// call sites of the one-ray-per-thread kernel (camera march, stencil, shadow
-// march) it overflows the instruction cache.  One out-of-line copy serves all
-// three (switch off with -DFR_PLAIN_INLINE_DE).
-template <int KIND, int U>
-__device__ __noinline__ float de_outlined(const DevReq &R, float3 p, int &trips)
-{
-    return de<KIND, U>(R, p, trips);
-}
-
-template <int KIND, int U>
-__device__ __forceinline__ float de_call(const DevReq &R, float3 p, int &trips)
-{
-#ifdef FR_PLAIN_INLINE_DE
-    return de<KIND, U>(R, p, trips);
-#else
-    if (KIND == 1) return de_outlined<KIND, U>(R, p, trips);
-    return de<KIND, U>(R, p, trips);
-#endif
-}
-
 // Sphere tracing (Listing "Julia Set ray cast"): from t0, d = DE(ro + t rd);
 // d < eps -> hit; t += min(d, max_step); t > t1 -> miss; running out of steps
 // inside the interval is reported as a hit at the current t.
@@ -40,7 +19,7 @@ __device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, flo
     bool hit = true;
     for (int i = 0; i < R.max_steps; i++) {
         int trips;
-        float d = de_call<KIND, U>(R, along(ro, rd, t), trips);
+        float d = de<KIND, U>(R, along(ro, rd, t), trips);
         steps++;
         if (COUNT) cnt.v[kStatOrbit] += trips;
         if (d < R.eps) break;
@@ -66,7 +45,7 @@ __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd
     float3 g = v3(0.0f, 0.0f, 0.0f);
     for (int k = 0; k < taps; k++) {
         int trips;
-        const float d = de_call<KIND, U>(R, tap_point(x, R.normal_mode, R.normal_h, k), trips);
+        const float d = de<KIND, U>(R, tap_point(x, R.normal_mode, R.normal_h, k), trips);
         tap_accum(g, R.normal_mode, R.normal_h, k, d);
         if (COUNT) cnt.v[kStatOrbit] += trips;
     }
