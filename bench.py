@@ -519,9 +519,39 @@ def main():
                                  "value": rays_per_step * args.steps * world / r["total_s"] / 1e6,
                                  "ms_per_step": r["total_s"] / args.steps * 1e3}
             res["speedup_vs_" + path] = r["total_s"] / total_s
+    if args.workload == "bulb_1080p" and not args.no_compare:
+        res["extras"] = bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step)
     if world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(scenes)
     print(json.dumps(res))
+
+
+def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step):
+    """Two more views of the same frame: (1) Eq. 1 evaluated without
+    transcendental calls (de Moivre powers; same image within the parity bar);
+    (2) eight consecutive frames of the camera orbit in one persistent launch,
+    where one frame's slowest pixels overlap the other frames' work."""
+    out = {}
+    alg = [dict(s, algebraic=True) for s in scenes]
+    counts = count_frame(api, torch, alg)
+    step = Renderer(api, F, alg, outs, "plain", api.current_stream())
+    for _ in range(args.warmup):
+        step()
+    times, total, _ = time_steps(torch, step, args.steps, tstream, flush)
+    out["algebraic_power"] = {"path": "plain", "ms_per_frame": total / args.steps * 1e3,
+                              "value": (counts[0] + counts[1]) * args.steps / total / 1e6,
+                              "unit": "Mrays/s", "orbit_iters": counts[5]}
+    frames = [W.bulb_1080p(10 + k) for k in range(8)]
+    fouts = [api.alloc_image(f) for f in frames]
+    fc = count_frame(api, torch, frames)
+    step = Renderer(api, F, frames, fouts, "persistent", api.current_stream())
+    for _ in range(args.warmup):
+        step()
+    times, total, _ = time_steps(torch, step, max(3, args.steps // 4), tstream, flush)
+    n = max(3, args.steps // 4)
+    out["eight_frames_in_flight"] = {"path": "persistent", "ms_per_8_frames": total / n * 1e3,
+                                     "value": (fc[0] + fc[1]) * n / total / 1e6, "unit": "Mrays/s"}
+    return out
 
 
 def ctypes_sizeof_inputs(F, n):

@@ -262,11 +262,21 @@ __device__ __forceinline__ float ipow(float r, int k)
     return res;
 }
 
+// r^(n-1): straight-line for the paper's n = 8, binary exponentiation otherwise
+__device__ __forceinline__ float rpow_nm1(float r, int n)
+{
+    if (n == 8) {
+        const float r2 = mul(r, r), r4 = mul(r2, r2);
+        return mul(mul(r4, r2), r);
+    }
+    return ipow(r, n - 1);
+}
+
 __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
 {
     const float nf = (float)n;
     const float r = sqrtf(o.m);
-    const float rn1 = ipow(r, n - 1);  // r^(n-1) (the listing's pow(sqrt(m), n-1))
+    const float rn1 = rpow_nm1(r, n);  // r^(n-1) (the listing's pow(sqrt(m), n-1))
     o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
@@ -331,13 +341,7 @@ __device__ __forceinline__ void bulb_step_alg(Orbit &o, float3 cpt, int n)
 {
     const float nf = (float)n;
     const float r = sqrtf(o.m);
-    float rn1;
-    if (n == 8) {
-        const float r2 = mul(r, r), r4 = mul(r2, r2);
-        rn1 = mul(mul(r4, r2), r);
-    } else {
-        rn1 = ipow(r, n - 1);
-    }
+    const float rn1 = rpow_nm1(r, n);
     o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
