@@ -33,10 +33,15 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # everything included (orbit step, DE epilogue, march update, stencils, camera
 # ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
 # divided by the iterations counted on the same scene (Mandelbulb n = 8 at
-# 480x270: 803.2 M / 3.187 M = 252; Julia p = 2 at 256x256: 364.9 M / 10.27 M
-# = 35.5).  The degree-3 Julia figure is the degree-2 one scaled by the ratio
-# of their orbit-step arithmetic (28 / 24).
-FLOPS_PER_ITER = {("julia", 2): 35.5, ("julia", 3): 41.4, ("bulb", 8): 252.0}
+# 1920x1080: 8.687 G / 50.88 M = 170.8, profiles/plain_kernel_mandelbulb_1080p.md;
+# Julia p = 2 at 256x256: 364.9 M / 10.27 M = 35.6).  The degree-3 Julia figure
+# is the degree-2 one scaled by the ratio of their orbit-step arithmetic
+# (28 / 24); other Mandelbulb powers take the n = 8 figure (same calls per step).
+FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5, ("bulb", 8): 170.8}
+# DRAM bytes of one launch of the dominant kernel, from the ncu capture of the
+# same command (dram__bytes_read.sum + dram__bytes_write.sum); the frame's
+# 16.6 MB of stores are still in the 129 MB L2 when the kernel ends.
+TRAFFIC = {("bulb_1080p", "plain"): 1034496 + 523008}
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32)
 
 
@@ -72,7 +77,7 @@ def workload(name: str, rank: int = 0):
 
 def flops_per_iter(scene) -> float:
     key = (scene["kind"], scene["p"] if scene["kind"] == "julia" else scene["n"])
-    return FLOPS_PER_ITER.get(key, FLOPS_PER_ITER[("bulb", 8)] if scene["kind"] == "bulb" else 35.5)
+    return FLOPS_PER_ITER.get(key, FLOPS_PER_ITER[("bulb", 8)] if scene["kind"] == "bulb" else 35.6)
 
 
 class ClockSampler:
@@ -500,7 +505,8 @@ def main():
         "per_step": {"rays": rays_per_step, "primary_rays": counts[0], "shadow_rays": counts[1],
                      "de_calls": de_per_step, "orbit_iters": iters_per_step},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": kern,
+                     "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, args.path)),
+                     "kernel": kern,
                      "flops_per_step": flops_per_step,
                      "peak_basis": "FP32 FFMA: %d SMs x %d lanes x 2 flops x %.0f MHz (max clock)" % (
                          sms, FP32_LANES_PER_SM, max_mhz),

@@ -139,8 +139,8 @@ typedef struct {
 } fr_bulb_params;
 
 /* Output buffers (device).  Any may be NULL except that at least one of rgba8,
- * rgba, depth, saved, stats must be given.  Alignment: rgba and saved 16 bytes,
- * the others 4 (stats 8). */
+ * rgba, depth, saved, stats, trap must be given.  Alignment: rgba, saved and
+ * trap 16 bytes, the others 4 (stats 8). */
 typedef struct {
     uint32_t *rgba8;             /* width*height packed colour                        */
     float *rgba;                 /* width*height*4 mean colour before quantisation     */
@@ -149,6 +149,12 @@ typedef struct {
                                  /* (1 hit, 2 cut face, 4 shadowed) as a float's bits; */
                                  /* the state fr_render_backward reads                 */
     unsigned long long *stats;   /* FR_NSTATS counters, ADDED to (zero them first)     */
+    float *trap;                 /* width*height*4 orbit-trap values of the DE at the  */
+                                 /* nearest hit point, (0,0,0,0) on a miss.  Mandelbulb: */
+                                 /* the listing's resColor = (final |w|^2, min |w.y|,   */
+                                 /* min |w.z|, min |w|^2); Julia: (iterations before    */
+                                 /* escape -- the listing's second output --, final    */
+                                 /* |z|^2, 0, 0).  One extra DE per hit pixel.          */
 } fr_image;
 
 /* One request of a batch.  `kind` selects which parameter block is read. */
@@ -170,6 +176,8 @@ typedef struct {
     int32_t persist_ctas_per_sm; /* resident CTAs per SM; 0 = as many as fit            */
     int32_t refill_threshold;    /* refill a warp once this many lanes are idle (1..32) */
     int32_t persist_unroll;      /* Julia orbit steps per scheduling round: 1, 2, 4, 8  */
+    int32_t single_kernel;       /* fr_render_julia/mandelbulb: 0 nested loops per thread,
+                                    1 lane state machine (one DE call site), no queue  */
 } fr_tuning;
 
 /* Render one quaternion Julia image with the one-ray-per-thread kernel

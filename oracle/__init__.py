@@ -88,6 +88,7 @@ class OrcOutputs(ctypes.Structure):
         ("stats", ctypes.c_void_p),
         ("rgba64", ctypes.c_void_p),
         ("depth64", ctypes.c_void_p),
+        ("trap", ctypes.c_void_p),
     ]
 
 
@@ -110,6 +111,7 @@ def lib():
             getattr(L, "orc_de_" + sfx).argtypes = [P(OrcScene), pr, pi, pi, pr]
             getattr(L, "orc_de_" + sfx).restype = r
             getattr(L, "orc_camera_ray_" + sfx).argtypes = [P(OrcScene), i, i, i, pr, pr]
+            getattr(L, "orc_trap_" + sfx).argtypes = [P(OrcScene), pr, pr]
             getattr(L, "orc_quantize_" + sfx).argtypes = [r]
             getattr(L, "orc_quantize_" + sfx).restype = ctypes.c_uint32
         L.orc_qpow_d.argtypes = [pd, i, pd]
@@ -182,7 +184,8 @@ def render(scene: dict, pixels=None, precision: str = "f32", threads: int = 1) -
     Returns numpy arrays: rgba (n,4) float32 mean colour, rgba8 (n,) uint32,
     depth (n,) float32 (+inf on a miss), flags (n,) int32 (1 hit, 2 cut face,
     4 shadowed), stats (n,5) int64 (primary DE calls, normal DE calls, shadow DE
-    calls, orbit iterations, shadow rays), and for f64 also rgba64 / depth64."""
+    calls, orbit iterations, shadow rays), trap (n,4) float32 orbit-trap colour
+    parameters at the nearest hit, and for f64 also rgba64 / depth64."""
     L = lib()
     s = scene_struct(scene)
     if pixels is None:
@@ -197,9 +200,11 @@ def render(scene: dict, pixels=None, precision: str = "f32", threads: int = 1) -
         "depth": np.zeros(n, np.float32),
         "flags": np.zeros(n, np.int32),
         "stats": np.zeros((n, 5), np.int64),
+        "trap": np.zeros((n, 4), np.float32),
     }
     out = OrcOutputs(res["rgba"].ctypes.data, res["rgba8"].ctypes.data, res["depth"].ctypes.data,
-                     res["flags"].ctypes.data, res["stats"].ctypes.data, None, None)
+                     res["flags"].ctypes.data, res["stats"].ctypes.data, None, None,
+                     res["trap"].ctypes.data)
     if precision == "f64":
         res["rgba64"] = np.zeros((n, 4), np.float64)
         res["depth64"] = np.zeros(n, np.float64)
@@ -315,6 +320,17 @@ def shade(scene, n, vis=1.0):
     n = _arr(n)
     o = np.zeros(4)
     lib().orc_shade_d(ctypes.byref(s), _ptr(n), float(vis), _ptr(o))
+    return o
+
+
+def trap(scene, p, precision: str = "f64"):
+    """Orbit-trap colour parameters of the DE at point p."""
+    dt, ct = (np.float64, ctypes.c_double) if precision == "f64" else (np.float32, ctypes.c_float)
+    fn = lib().orc_trap_d if precision == "f64" else lib().orc_trap_f
+    s = scene_struct(scene)
+    pp = _arr(p, dt)
+    o = np.zeros(4, dt)
+    fn(ctypes.byref(s), _ptr(pp, ct), _ptr(o, ct))
     return o
 
 

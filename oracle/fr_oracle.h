@@ -82,6 +82,9 @@ typedef struct {
                                  orbit iterations, shadow rays             */
     double *rgba64;           /* n x 4, same as rgba at the render precision (double build) */
     double *depth64;          /* n */
+    float *trap;              /* n x 4, orbit-trap colour parameters at the nearest hit
+                                 (Mandelbulb listing: (m, min|w.y|, min|w.z|, min m);
+                                 Julia listing: (iterations before escape, |z|^2, 0, 0)) */
 } orc_outputs;
 
 /* Render pixels[i] (linear index y*width + x) for i < n_pixels; pixels == NULL
@@ -124,6 +127,9 @@ void orc_normal_field_d(int kind, const double *prm, const double p[3], int mode
                         const double rd[3], double n_out[3]);
 /* Lambert closed-hit shading of one sample and the 8-bit quantiser */
 void orc_shade_d(const orc_scene *s, const double n[3], double vis, double rgba_out[4]);
+/* orbit-trap colour parameters of the DE at a point (see orc_outputs.trap) */
+void orc_trap_d(const orc_scene *s, const double p[3], double out[4]);
+void orc_trap_f(const orc_scene *s, const float p[3], float out[4]);
 uint32_t orc_quantize_d(double x);
 uint32_t orc_quantize_f(float x);
 

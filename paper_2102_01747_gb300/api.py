@@ -78,10 +78,10 @@ def light_struct(scene: dict) -> F.fr_light:
 
 
 def alloc_image(scene: dict, device="cuda", rgba8=True, rgba=False, depth=True, saved=False,
-                stats=False) -> dict:
+                stats=False, trap=False) -> dict:
     """Output tensors for one scene: rgba8 (H, W) int32 holding the packed
     uint32, rgba (H, W, 4) float32, depth (H, W) float32, saved (H, W, 4)
-    float32, stats (6,) int64 (zeroed)."""
+    float32, stats (6,) int64 (zeroed), trap (H, W, 4) float32."""
     H, W = scene["camera"]["height"], scene["camera"]["width"]
     out = {}
     if rgba8:
@@ -94,6 +94,8 @@ def alloc_image(scene: dict, device="cuda", rgba8=True, rgba=False, depth=True, 
         out["saved"] = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     if stats:
         out["stats"] = torch.zeros(F.FR_NSTATS, dtype=torch.int64, device=device)
+    if trap:
+        out["trap"] = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     return out
 
 
@@ -111,6 +113,7 @@ def image_struct(tensors: dict) -> F.fr_image:
     img.depth = _ptr(tensors.get("depth"))
     img.saved = _ptr(tensors.get("saved"))
     img.stats = _ptr(tensors.get("stats"))
+    img.trap = _ptr(tensors.get("trap"))
     return img
 
 

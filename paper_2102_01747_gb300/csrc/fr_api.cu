@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 64, 0, 16, 4};
+fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0};
 
 fr_tuning tuning()
 {
@@ -188,16 +188,17 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
     }
 
     if (!need_out) return FR_OK;
-    if (!out->rgba8 && !out->rgba && !out->depth && !out->saved && !out->stats)
+    if (!out->rgba8 && !out->rgba && !out->depth && !out->saved && !out->stats && !out->trap)
         return fail(FR_EINVAL, "image has no output buffer");
     if (!aligned(out->rgba8, 4) || !aligned(out->depth, 4) || !aligned(out->rgba, 16) ||
-        !aligned(out->saved, 16) || !aligned(out->stats, 8))
-        return fail(FR_EINVAL, "output buffer misaligned (rgba/saved 16 B, rgba8/depth 4 B, stats 8 B)");
+        !aligned(out->saved, 16) || !aligned(out->stats, 8) || !aligned(out->trap, 16))
+        return fail(FR_EINVAL, "output buffer misaligned (rgba/saved/trap 16 B, rgba8/depth 4 B, stats 8 B)");
     R.rgba8 = out->rgba8;
     R.rgba = reinterpret_cast<float4 *>(out->rgba);
     R.depth = out->depth;
     R.saved = reinterpret_cast<float4 *>(out->saved);
     R.stats = out->stats;
+    R.trap = reinterpret_cast<float4 *>(out->trap);
     return FR_OK;
 }
 
@@ -241,9 +242,27 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
         return fail(FR_EINVAL, "persist_ctas_per_sm outside 0..32");
     if (t->refill_threshold < 1 || t->refill_threshold > 32)
         return fail(FR_EINVAL, "refill_threshold outside 1..32");
+    if (t->single_kernel != 0 && t->single_kernel != 1) return fail(FR_EINVAL, "single_kernel must be 0 or 1");
     std::lock_guard<std::mutex> lk(g_tuning_mu);
     g_tuning = *t;
     return FR_OK;
+}
+
+// one request through the configured single-request kernel
+static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
+{
+    const fr_tuning tu = tuning();
+    if (tu.single_kernel == 1) {
+        static thread_local fr::BatchArgs A;
+        A.reqs[0] = R;
+        A.reqs[0].unit_begin = 0;
+        A.n_reqs = 1;
+        A.total_units = R.n_units;
+        A.refill_threshold = 1;
+        A.queue = nullptr;
+        return launched(fr::launch_lanes(A, tu.plain_block, tu.persist_unroll, count, (cudaStream_t)stream));
+    }
+    return launched(fr::launch_plain(R, tu.plain_block, tu.plain_unroll, count, (cudaStream_t)stream));
 }
 
 FR_API fr_status fr_render_julia(const fr_julia_params *params, const fr_plane *plane,
@@ -255,9 +274,7 @@ FR_API fr_status fr_render_julia(const fr_julia_params *params, const fr_plane *
     fr_status st = resolve_julia(R, params);
     if (st != FR_OK) return st;
     if ((st = resolve_common(R, plane, camera, light, out)) != FR_OK) return st;
-    const fr_tuning tu = tuning();
-    return launched(fr::launch_plain(R, tu.plain_block, tu.plain_unroll, out->stats != nullptr,
-                                     (cudaStream_t)stream));
+    return launch_single(R, out->stats != nullptr, stream);
 }
 
 FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_plane *plane,
@@ -269,9 +286,7 @@ FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_pla
     fr_status st = resolve_bulb(R, params);
     if (st != FR_OK) return st;
     if ((st = resolve_common(R, plane, camera, light, out)) != FR_OK) return st;
-    const fr_tuning tu = tuning();
-    return launched(fr::launch_plain(R, tu.plain_block, tu.plain_unroll, out->stats != nullptr,
-                                     (cudaStream_t)stream));
+    return launch_single(R, out->stats != nullptr, stream);
 }
 
 // one 256-byte slot (queue head) per launch of up to kMaxReqPerLaunch requests

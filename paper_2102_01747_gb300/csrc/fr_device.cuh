@@ -73,6 +73,7 @@ struct __align__(16) DevReq {
     float *depth;
     float4 *saved;
     unsigned long long *stats;
+    float4 *trap;
     long long unit_begin; // first queue unit of this request inside a batch
     long long n_units;    // tiles * 32
 };
@@ -444,6 +445,44 @@ __device__ __forceinline__ float de(const DevReq &R, float3 p, int &trips)
     return bulb_de<U>(R.power, R.max_iter, R.esc2, p, R.bulb_alg, trips);
 }
 
+// ------------------------------------------------------------------ orbit traps
+// Colour parameters of the DE at a point, as the listings hand them to the
+// closest-hit stage.  Mandelbulb (Listing "Mandelbulb distance"): the running
+// minimum of (|w.x|, |w.y|, |w.z|, m), started at w0 = c and updated after
+// each step with the new w and the m of the step before, returned as
+// (final m, min |w.y|, min |w.z|, min m).  Julia (Listing "Julia Set
+// distance"): the count of steps that did not escape, with the final |z|^2.
+__device__ __forceinline__ float4 orbit_trap(const DevReq &R, float3 p)
+{
+    Orbit o;
+    if (R.kind == 0) {
+        julia_init(o, p, R.slice_w);
+        int n = 0;
+        for (int k = 0; k < R.max_iter; k++) {
+            if (R.power == 2)
+                julia2_step(o, R.c);
+            else
+                julia3_step(o, R.c);
+            if (o.m > R.esc2) break;
+            n++;
+        }
+        return make_float4((float)n, o.m, 0.0f, 0.0f);
+    }
+    bulb_init(o, p);
+    float4 t = make_float4(fabsf(o.a), fabsf(o.b), fabsf(o.c), o.m);
+    for (int k = 0; k < R.max_iter; k++) {
+        const float m_prev = o.m;
+        if (R.bulb_alg)
+            bulb_step_alg(o, p, R.power);
+        else
+            bulb_step(o, p, R.power);
+        t = make_float4(fminf(t.x, fabsf(o.a)), fminf(t.y, fabsf(o.b)), fminf(t.z, fabsf(o.c)),
+                        fminf(t.w, m_prev));
+        if (o.m > R.esc2) break;
+    }
+    return make_float4(o.m, t.y, t.z, t.w);
+}
+
 // ------------------------------------------------------------------ normal stencils
 // Tap k of the stencil around x and its contribution to the gradient sum g.
 // Tetrahedral (Eq. 5, Listing "Normal calculation"): taps x + h nu_k with
@@ -562,6 +601,7 @@ __device__ __forceinline__ void store_pixel(const DevReq &R, int px, int py, flo
     if (R.rgba) R.rgba[idx] = acc;
     if (R.depth) R.depth[idx] = dmin;
     if (R.saved) R.saved[idx] = make_float4(xhit.x, xhit.y, xhit.z, __uint_as_float(flags));
+    if (R.trap) R.trap[idx] = (flags & kFlagHit) ? orbit_trap(R, xhit) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 }  // namespace fr

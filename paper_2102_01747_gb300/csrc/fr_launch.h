@@ -38,6 +38,9 @@ cudaError_t launch_backward(const BwdArgs &A, cudaStream_t s);
 // one-ray-per-thread forward kernel for one request
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s);
 
+// lane-state-machine forward kernel without the queue: one pixel per lane, all tiles launched
+cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, cudaStream_t s);
+
 // persistent forward kernel over A.n_reqs requests (memset of the queue head + launch)
 cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int unroll, bool count,
                            cudaStream_t s);

@@ -113,6 +113,8 @@ __device__ __forceinline__ void store_and_idle(Lane &S, const DevReq &R, PixCoun
         }
         sv[3] = __uint_as_float(L_pflags(S));
     }
+    // the trap of the nearest hit was written when it was found
+    if (R.trap && !(L_pflags(S) & kFlagHit)) R.trap[idx] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     L_set_phase(S, PH_IDLE);
     if (COUNT && R.stats) {
 #pragma unroll
@@ -166,6 +168,7 @@ __device__ __forceinline__ void finish_sample(Lane &S, const DevReq &R, float4 c
                 sv[1] = S.x.y;
                 sv[2] = S.x.z;
             }
+            if (R.trap) R.trap[pixel_index(R, S)] = orbit_trap(R, S.x);
         }
         S.meta |= L_sflags(S) << 24;
     }
@@ -297,7 +300,11 @@ __device__ __forceinline__ void start_pixel(Lane &S, long long u, const DevReq *
 #define FR_PERSIST_MIN_BLOCKS 2
 #endif
 
-template <int KJ, bool COUNT>
+// REFILL = false is the same lane state machine without the queue: every warp
+// takes the 32 pixel slots of one tile at launch (grid = all tiles) and ends
+// when its lanes are done.  Lanes of different phases still share one DE code
+// path and never wait for each other's orbits, but nothing is refilled.
+template <int KJ, bool COUNT, bool REFILL>
 __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(const __grid_constant__ BatchArgs A)
 {
     extern __shared__ float4 smem[];
@@ -323,6 +330,11 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
 #pragma unroll
     for (int k = 0; k < kNStats; k++) pc.v[k] = 0;
     bool exhausted = false;
+    if (!REFILL) {
+        const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+        if ((unsigned long long)u < total) start_pixel<COUNT>(S, u, sreq, sbegin, nq, pc);
+        exhausted = true;
+    }
 
     for (;;) {
         // ---- refill idle lanes (warp-uniform control flow): one atomicAdd takes
@@ -384,21 +396,26 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
     }
 }
 
-template <int KJ, bool COUNT>
+template <int KJ, bool COUNT, bool REFILL>
 static cudaError_t launch_persist_t(const BatchArgs &A, int block, int ctas_per_sm, cudaStream_t s)
 {
     const size_t smem = (size_t)A.n_reqs * sizeof(DevReq);
+    if (!REFILL) {
+        const long long grid = (A.total_units + block - 1) / block;
+        persist_kernel<KJ, COUNT, false><<<(unsigned)grid, block, smem, s>>>(A);
+        return cudaGetLastError();
+    }
     int dev = 0, sms = 0, fit = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, persist_kernel<KJ, COUNT>, block, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, persist_kernel<KJ, COUNT, true>, block, smem)) !=
         cudaSuccess)
         return e;
     if (fit < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < fit) ? ctas_per_sm : fit;
     if ((e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    persist_kernel<KJ, COUNT><<<sms * per_sm, block, smem, s>>>(A);
+    persist_kernel<KJ, COUNT, true><<<sms * per_sm, block, smem, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -407,11 +424,19 @@ static_assert(sizeof(BatchArgs) <= 32764, "the request table must fit the kernel
 cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int unroll, bool count,
                            cudaStream_t s)
 {
-    if (count) return launch_persist_t<4, true>(A, block, ctas_per_sm, s);
-    if (unroll == 8) return launch_persist_t<8, false>(A, block, ctas_per_sm, s);
-    if (unroll == 4) return launch_persist_t<4, false>(A, block, ctas_per_sm, s);
-    if (unroll == 2) return launch_persist_t<2, false>(A, block, ctas_per_sm, s);
-    return launch_persist_t<1, false>(A, block, ctas_per_sm, s);
+    if (count) return launch_persist_t<4, true, true>(A, block, ctas_per_sm, s);
+    if (unroll == 8) return launch_persist_t<8, false, true>(A, block, ctas_per_sm, s);
+    if (unroll == 4) return launch_persist_t<4, false, true>(A, block, ctas_per_sm, s);
+    if (unroll == 2) return launch_persist_t<2, false, true>(A, block, ctas_per_sm, s);
+    return launch_persist_t<1, false, true>(A, block, ctas_per_sm, s);
+}
+
+cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, cudaStream_t s)
+{
+    if (count) return launch_persist_t<4, true, false>(A, block, 0, s);
+    if (unroll == 8) return launch_persist_t<8, false, false>(A, block, 0, s);
+    if (unroll == 2) return launch_persist_t<2, false, false>(A, block, 0, s);
+    return launch_persist_t<4, false, false>(A, block, 0, s);
 }
 
 }  // namespace fr

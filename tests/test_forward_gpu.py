@@ -100,8 +100,9 @@ def test_jittered_samples(api, orc):
     check(api, orc, s)
 
 
-@pytest.mark.parametrize("block,unroll", [(32, 1), (64, 2), (256, 4), (128, 1)])
-def test_launch_shapes_give_identical_images(api, block, unroll):
+@pytest.mark.parametrize("block,unroll,single", [(32, 1, 0), (64, 2, 0), (256, 4, 0), (128, 1, 0),
+                                                (128, 1, 1), (64, 2, 1), (256, 8, 1)])
+def test_launch_shapes_give_identical_images(api, block, unroll, single):
     from paper_2102_01747_gb300 import _ffi as F
 
     old = F.fr_get_tuning()
@@ -110,13 +111,18 @@ def test_launch_shapes_give_identical_images(api, block, unroll):
     j = W.julia_256(130, 70)
     ref = (gpu(api, s), gpu(api, j))
     t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
-    t.plain_block, t.plain_unroll = block, unroll
+    t.plain_block, t.single_kernel = block, single
+    if single:
+        t.persist_unroll = unroll  # the lane state machine's Julia steps per round
+    else:
+        t.plain_unroll = unroll
     assert F.fr_set_tuning(t) == F.FR_OK
     try:
         for scene, r in zip((s, j), ref):
             g = gpu(api, scene)
-            # every rounding step is explicit, so block shape and unroll depth
-            # cannot change a single bit
+            # every rounding step is explicit, so neither the block shape, the
+            # unroll depth nor the kernel (nested loops or lane state machine)
+            # can change a single bit
             assert np.array_equal(g["rgba8"], r["rgba8"])
             assert np.array_equal(g["depth"], r["depth"])
     finally:
@@ -182,3 +188,25 @@ def test_algebraic_power_matches_oracle(api, orc, n):
     s["algebraic"] = True
     res, _, _ = check(api, orc, s)
     assert res["hits"] > 1000
+
+
+@pytest.mark.parametrize("kind", ["julia", "bulb"])
+def test_orbit_trap_output(api, orc, kind):
+    """The orbit-trap colour parameters at the nearest hit point against the oracle's."""
+    import torch
+
+    s = W.julia_256(120, 90) if kind == "julia" else W.bulb_1080p(14, 160, 90)
+    out = api.render(s, rgba8=True, depth=True, trap=True)
+    torch.cuda.synchronize()
+    g = out["trap"].cpu().numpy().reshape(-1, 4)
+    o = orc.render(s, precision="f32", threads=THREADS)
+    gd = out["depth"].cpu().numpy().reshape(-1)
+    both = np.isfinite(gd) & np.isfinite(o["depth"])
+    miss = ~np.isfinite(gd)
+    assert np.all(g[miss] == 0)
+    close = np.all(np.abs(g[both] - o["trap"][both]) <= 1e-3 * np.abs(o["trap"][both]) + 1e-6, 1)
+    assert both.sum() > 1000 and np.mean(close) >= 0.98, np.mean(close)
+    # the persistent kernel writes the same values
+    b = api.render_batch([s], rgba8=True, depth=True, trap=True)[0]
+    torch.cuda.synchronize()
+    assert np.array_equal(b["trap"].cpu().numpy(), out["trap"].cpu().numpy())

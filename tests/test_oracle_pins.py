@@ -530,3 +530,35 @@ def test_f32_oracle_close_to_f64(orc, which):
     ca = np.stack([(a["rgba8"] >> (8 * k)) & 255 for k in range(4)], -1).astype(int)
     cb = np.stack([(b["rgba8"] >> (8 * k)) & 255 for k in range(4)], -1).astype(int)
     assert np.mean(np.all(np.abs(ca - cb) <= 3, -1)) >= 0.99
+
+
+# ------------------------------------------------------ orbit traps (listing colour outputs)
+def test_julia_trap_is_escape_count(orc):
+    """Julia: the listing's second output is the number of non-escaping steps; on
+    span{1, i} it equals the complex orbit's count and final |z|^2 bit for bit."""
+    rng = np.random.default_rng(31)
+    s = W.julia_256(8, 8)
+    c = complex(-0.2, 0.6)
+    s["c"] = (c.real, c.imag, 0.0, 0.0)
+    for x, y in rng.uniform(-1.5, 1.5, (300, 2)):
+        t = orc.trap(s, [x, y, 0.0])
+        _, n, _, m2 = _complex_de(complex(x, y), c, s["max_iter"], s["escape_r2"])
+        assert t[0] == n and t[1] == m2 and t[2] == 0 and t[3] == 0
+
+
+def test_bulb_trap_on_polar_axis(orc):
+    """On the +y axis Eq. 1 maps (0, y, 0) to (0, y^n, 0), so the orbit is the scalar
+    recursion y <- y^n + y0 and the trap is (final y^2, y0, 0, y0^2)."""
+    s = W.bulb_1080p(0, 8, 8)
+    for y0 in (0.3, 0.6, 0.9, 1.05):
+        for n in (2, 3, 8):
+            s["n"] = n
+            y, m = y0, y0 * y0
+            for _ in range(s["max_iter"]):
+                y = y**n + y0
+                m = y * y
+                if m > s["bailout"] ** 2:
+                    break
+            t = orc.trap(s, [0.0, y0, 0.0])
+            assert abs(t[0] - m) <= 1e-12 * max(1.0, m)
+            assert t[1] == y0 and t[2] == 0.0 and abs(t[3] - y0 * y0) <= 1e-15
