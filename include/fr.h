@@ -62,7 +62,7 @@ typedef enum {
 } fr_status;
 
 enum { FR_KIND_JULIA = 0, FR_KIND_BULB = 1 };
-enum { FR_NORMAL_TETRA = 0, FR_NORMAL_CENTRAL = 1 };
+enum { FR_NORMAL_TETRA = 0, FR_NORMAL_CENTRAL = 1, FR_NORMAL_ANALYTIC = 2 };
 
 /* indices into fr_image.stats */
 enum {
@@ -117,7 +117,10 @@ typedef struct {
     int32_t max_steps;       /* march step cap, 1..100000 (listing: 1024)         */
     float eps;               /* hit threshold kPrecis, > 0                        */
     float max_step;          /* step clamp (listing: 0.2), > 0                    */
-    int32_t normal_mode;     /* FR_NORMAL_TETRA or FR_NORMAL_CENTRAL              */
+    int32_t normal_mode;     /* FR_NORMAL_TETRA, FR_NORMAL_CENTRAL, or FR_NORMAL_ANALYTIC:
+                                grad d = grad G / |grad G| on the set (Sec. 2), from the
+                                orbit's derivative carried alongside it (no stencil;
+                                not accepted by fr_render_backward)                 */
     float normal_h;          /* stencil size; 0 = 0.5773*eps (tetra), 1e-4 (central) */
 } fr_julia_params;
 

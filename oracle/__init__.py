@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 SOURCES = ["fr_oracle.c", "fr_oracle_body.inc", "fr_oracle_grad.inc", "fr_oracle.h"]
 
 JULIA, BULB = 0, 1
-NORMAL_TETRA, NORMAL_CENTRAL = 0, 1
+NORMAL_TETRA, NORMAL_CENTRAL, NORMAL_ANALYTIC = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -112,6 +112,7 @@ def lib():
             getattr(L, "orc_de_" + sfx).restype = r
             getattr(L, "orc_camera_ray_" + sfx).argtypes = [P(OrcScene), i, i, i, pr, pr]
             getattr(L, "orc_trap_" + sfx).argtypes = [P(OrcScene), pr, pr]
+            getattr(L, "orc_normal_scene_" + sfx).argtypes = [P(OrcScene), pr, pr, pr]
             getattr(L, "orc_quantize_" + sfx).argtypes = [r]
             getattr(L, "orc_quantize_" + sfx).restype = ctypes.c_uint32
         L.orc_qpow_d.argtypes = [pd, i, pd]
@@ -154,7 +155,8 @@ def scene_struct(scene: dict) -> OrcScene:
     s.max_steps = int(scene["max_steps"])
     s.eps = float(scene["eps"])
     s.max_step = float(scene["max_step"])
-    s.normal_mode = NORMAL_TETRA if scene["normal_mode"] == "tetra" else NORMAL_CENTRAL
+    s.normal_mode = {"tetra": NORMAL_TETRA, "central": NORMAL_CENTRAL,
+                     "analytic": NORMAL_ANALYTIC}[scene["normal_mode"]]
     s.normal_h = float(scene["normal_h"])
     pl = scene.get("plane")
     s.plane_enabled = 1 if pl else 0
@@ -320,6 +322,17 @@ def shade(scene, n, vis=1.0):
     n = _arr(n)
     o = np.zeros(4)
     lib().orc_shade_d(ctypes.byref(s), _ptr(n), float(vis), _ptr(o))
+    return o
+
+
+def normal_scene(scene, p, rd=(0.0, 0.0, -1.0), precision: str = "f64"):
+    """Unit normal at p by the scene's normal mode."""
+    dt, ct = (np.float64, ctypes.c_double) if precision == "f64" else (np.float32, ctypes.c_float)
+    fn = lib().orc_normal_scene_d if precision == "f64" else lib().orc_normal_scene_f
+    s = scene_struct(scene)
+    pp, rr = _arr(p, dt), _arr(rd, dt)
+    o = np.zeros(3, dt)
+    fn(ctypes.byref(s), _ptr(pp, ct), _ptr(rr, ct), _ptr(o, ct))
     return o
 
 

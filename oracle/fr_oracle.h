@@ -34,7 +34,7 @@ extern "C" {
 #endif
 
 enum { ORC_JULIA = 0, ORC_BULB = 1 };
-enum { ORC_NORMAL_TETRA = 0, ORC_NORMAL_CENTRAL = 1 };
+enum { ORC_NORMAL_TETRA = 0, ORC_NORMAL_CENTRAL = 1, ORC_NORMAL_ANALYTIC = 2 };
 
 /* One render request.  All reals are doubles; the float build rounds them. */
 typedef struct {
@@ -127,6 +127,10 @@ void orc_normal_field_d(int kind, const double *prm, const double p[3], int mode
                         const double rd[3], double n_out[3]);
 /* Lambert closed-hit shading of one sample and the 8-bit quantiser */
 void orc_shade_d(const orc_scene *s, const double n[3], double vis, double rgba_out[4]);
+/* unit normal at a point by the scene's normal mode (tetrahedral, central, or
+ * -- Julia only -- analytic); rd is the fallback direction's ray */
+void orc_normal_scene_d(const orc_scene *s, const double p[3], const double rd[3], double n[3]);
+void orc_normal_scene_f(const orc_scene *s, const float p[3], const float rd[3], float n[3]);
 /* orbit-trap colour parameters of the DE at a point (see orc_outputs.trap) */
 void orc_trap_d(const orc_scene *s, const double p[3], double out[4]);
 void orc_trap_f(const orc_scene *s, const float p[3], float out[4]);

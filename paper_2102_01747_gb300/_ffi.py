@@ -15,7 +15,7 @@ c_int32, c_uint32, c_float, c_void_p = ctypes.c_int32, ctypes.c_uint32, ctypes.c
 
 FR_OK, FR_EINVAL, FR_ECUDA, FR_ETIMEOUT, FR_ENOMEM, FR_ENOTIMPL = range(6)
 FR_KIND_JULIA, FR_KIND_BULB = 0, 1
-FR_NORMAL_TETRA, FR_NORMAL_CENTRAL = 0, 1
+FR_NORMAL_TETRA, FR_NORMAL_CENTRAL, FR_NORMAL_ANALYTIC = 0, 1, 2
 (FR_STAT_PRIMARY_RAYS, FR_STAT_SHADOW_RAYS, FR_STAT_PRIMARY_DE, FR_STAT_NORMAL_DE,
  FR_STAT_SHADOW_DE, FR_STAT_ORBIT_ITERS, FR_NSTATS) = range(7)
 STATUS_NAMES = {0: "FR_OK", 1: "FR_EINVAL", 2: "FR_ECUDA", 3: "FR_ETIMEOUT", 4: "FR_ENOMEM",

@@ -27,7 +27,8 @@ def julia_params(scene: dict) -> F.fr_julia_params:
     p.max_steps = int(scene["max_steps"])
     p.eps = float(scene["eps"])
     p.max_step = float(scene["max_step"])
-    p.normal_mode = F.FR_NORMAL_TETRA if scene["normal_mode"] == "tetra" else F.FR_NORMAL_CENTRAL
+    p.normal_mode = {"tetra": F.FR_NORMAL_TETRA, "central": F.FR_NORMAL_CENTRAL,
+                     "analytic": F.FR_NORMAL_ANALYTIC}[scene["normal_mode"]]
     p.normal_h = float(scene["normal_h"])
     return p
 

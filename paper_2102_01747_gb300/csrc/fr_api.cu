@@ -75,7 +75,7 @@ fr_status resolve_march(fr::DevReq &R, int max_iter, float bound_radius, int max
     if (!(eps > 0.0f) || !std::isfinite(eps)) return fail(FR_EINVAL, "eps must be positive and finite");
     if (!(max_step > 0.0f) || !std::isfinite(max_step))
         return fail(FR_EINVAL, "max_step must be positive and finite");
-    if (normal_mode != FR_NORMAL_TETRA && normal_mode != FR_NORMAL_CENTRAL)
+    if (normal_mode != FR_NORMAL_TETRA && normal_mode != FR_NORMAL_CENTRAL && normal_mode != FR_NORMAL_ANALYTIC)
         return fail(FR_EINVAL, "normal_mode %d unknown", normal_mode);
     if (!(normal_h >= 0.0f) || !std::isfinite(normal_h))
         return fail(FR_EINVAL, "normal_h must be >= 0 and finite");
@@ -113,6 +113,8 @@ fr_status resolve_bulb(fr::DevReq &R, const fr_bulb_params *P)
     if (P->n < 2 || P->n > 16) return fail(FR_EINVAL, "mandelbulb power n=%d outside 2..16", P->n);
     if (!(P->bailout > 0.0f) || !std::isfinite(P->bailout))
         return fail(FR_EINVAL, "bailout must be positive and finite");
+    if (P->normal_mode == FR_NORMAL_ANALYTIC)
+        return fail(FR_EINVAL, "the analytic normal is implemented for the Julia set only");
     R.kind = FR_KIND_BULB;
     R.c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     R.power = P->n;
@@ -355,6 +357,8 @@ FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plan
     std::memset(&A, 0, sizeof A);
     fr_status st = resolve_julia(A.R, params);
     if (st != FR_OK) return st;
+    if (params->normal_mode == FR_NORMAL_ANALYTIC)
+        return fail(FR_EINVAL, "backward supports the tetrahedral and central normals");
     if (params->max_iter > fr::kMaxBwdIter)
         return fail(FR_EINVAL, "backward keeps at most %d orbit iterations (max_iter %d)", fr::kMaxBwdIter,
                     params->max_iter);

@@ -483,6 +483,65 @@ __device__ __forceinline__ float4 orbit_trap(const DevReq &R, float3 p)
     return make_float4(o.m, t.y, t.z, t.w);
 }
 
+// ------------------------------------------------------------------ analytic normal
+// Sec. 2: on the set grad d = grad G / |grad G|, and grad G at x is parallel to
+// J^T z_N, J = dz_N / dz_0 (G = lim log|z_N| / p^N).  The three slice
+// directions of J are carried through the orbit as tangent quaternions
+// (forward mode): t <- D(z^p)[t], with
+//   p = 2: D[t] = z t + t z = (2(a ta - v.tv), 2(a tv + ta v))        z = (a, v)
+//   p = 3: D[t] = ((3a^2 - 3|v|^2) ta - 6a v.tv, (6a ta - 2 v.tv) v + (3a^2 - |v|^2) tv)
+// and the gradient is (z_N . t_x, z_N . t_y, z_N . t_z).  The orbit runs with
+// the same step function and stop rule as the DE.
+__device__ __forceinline__ void tangent_step(float4 &t, const Orbit &o, int p)
+{
+    const float vdt = fmaf(o.d, t.w, fmaf(o.c, t.z, mul(o.b, t.y)));
+    if (p == 2) {
+        const float na = mul(2.0f, fmaf(o.a, t.x, -vdt));
+        t.y = mul(2.0f, fmaf(o.a, t.y, mul(t.x, o.b)));
+        t.z = mul(2.0f, fmaf(o.a, t.z, mul(t.x, o.c)));
+        t.w = mul(2.0f, fmaf(o.a, t.w, mul(t.x, o.d)));
+        t.x = na;
+        return;
+    }
+    const float v2 = fmaf(o.d, o.d, fmaf(o.c, o.c, mul(o.b, o.b)));
+    const float a2 = mul(o.a, o.a);
+    const float f = fmaf(3.0f, a2, -v2);
+    const float s = fmaf(6.0f * o.a, t.x, mul(-2.0f, vdt));  // coefficient of v
+    const float na = fmaf(mul(3.0f, sub(a2, v2)), t.x, mul(-6.0f * o.a, vdt));
+    t.y = fmaf(s, o.b, mul(f, t.y));
+    t.z = fmaf(s, o.c, mul(f, t.z));
+    t.w = fmaf(s, o.d, mul(f, t.w));
+    t.x = na;
+}
+
+__device__ __forceinline__ float3 julia_analytic_normal(const DevReq &R, float3 x, float3 rd, int &trips)
+{
+    Orbit o;
+    julia_init(o, x, R.slice_w);
+    float4 tx = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    float4 ty = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+    float4 tz = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+    int i = 0;
+    for (int k = 0; k < R.max_iter; k++) {
+        tangent_step(tx, o, R.power);
+        tangent_step(ty, o, R.power);
+        tangent_step(tz, o, R.power);
+        if (R.power == 2)
+            julia2_step(o, R.c);
+        else
+            julia3_step(o, R.c);
+        i++;
+        if (o.m > R.esc2) break;
+    }
+    trips = i;
+    const float3 g = v3(fmaf(o.d, tx.w, fmaf(o.c, tx.z, fmaf(o.b, tx.y, mul(o.a, tx.x)))),
+                        fmaf(o.d, ty.w, fmaf(o.c, ty.z, fmaf(o.b, ty.y, mul(o.a, ty.x)))),
+                        fmaf(o.d, tz.w, fmaf(o.c, tz.z, fmaf(o.b, tz.y, mul(o.a, tz.x)))));
+    const float l = sqrtf(dot3(g, g));
+    if (!(l > 0.0f) || !isfinite(l)) return v3(-rd.x, -rd.y, -rd.z);
+    return v3(dvd(g.x, l), dvd(g.y, l), dvd(g.z, l));
+}
+
 // ------------------------------------------------------------------ normal stencils
 // Tap k of the stencil around x and its contribution to the gradient sum g.
 // Tetrahedral (Eq. 5, Listing "Normal calculation"): taps x + h nu_k with

@@ -256,6 +256,16 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
         after_normal<COUNT>(S, R, pc);
         return;
     }
+    if (R.kind == 0 && R.normal_mode == 2) {  // analytic normal: one orbit with tangents, no stencil
+        int trips;
+        S.g = julia_analytic_normal(R, S.x, S.rd, trips);
+        if (COUNT) {
+            pc.v[kStatNormalDE] += 1;
+            pc.v[kStatOrbit] += trips;
+        }
+        after_normal<COUNT>(S, R, pc);
+        return;
+    }
     L_set_phase(S, PH_NORMAL);
     L_set_tap(S, 0);
     S.g = v3(0.0f, 0.0f, 0.0f);

@@ -41,6 +41,15 @@ __device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, flo
 template <int KIND, int U, bool COUNT>
 __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd, Counters &cnt)
 {
+    if (KIND == 0 && R.normal_mode == 2) {
+        int trips;
+        const float3 n = julia_analytic_normal(R, x, rd, trips);
+        if (COUNT) {
+            cnt.v[kStatNormalDE] += 1;
+            cnt.v[kStatOrbit] += trips;
+        }
+        return n;
+    }
     const int taps = R.normal_mode == 0 ? 4 : 6;
     float3 g = v3(0.0f, 0.0f, 0.0f);
     for (int k = 0; k < taps; k++) {

@@ -204,9 +204,30 @@ def test_orbit_trap_output(api, orc, kind):
     both = np.isfinite(gd) & np.isfinite(o["depth"])
     miss = ~np.isfinite(gd)
     assert np.all(g[miss] == 0)
+    if kind == "bulb":
+        # the trap is a chaotic function of the point wherever the orbit stays bounded
+        # (the cut face shows interior points); compare where the orbit escapes
+        both &= (o["flags"] & 2) == 0
+        both &= o["trap"][:, 0] > s["bailout"] ** 2
     close = np.all(np.abs(g[both] - o["trap"][both]) <= 1e-3 * np.abs(o["trap"][both]) + 1e-6, 1)
-    assert both.sum() > 1000 and np.mean(close) >= 0.98, np.mean(close)
+    assert both.sum() > 500 and np.mean(close) >= 0.98, (both.sum(), np.mean(close))
     # the persistent kernel writes the same values
     b = api.render_batch([s], rgba8=True, depth=True, trap=True)[0]
     torch.cuda.synchronize()
     assert np.array_equal(b["trap"].cpu().numpy(), out["trap"].cpu().numpy())
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_analytic_normal_render(api, orc, p):
+    """Julia renders shaded with the analytic normal (Sec. 2) against the oracle."""
+    s = W.julia_256(160, 120)
+    s.update(p=p, escape_r2=256.0 if p == 3 else 16.0, max_iter=11, normal_mode="analytic")
+    s["light"]["shadows"] = True
+    res, _, _ = check(api, orc, s)
+    assert res["hits"] > 3000
+    import torch
+
+    b = api.render_batch([s], rgba8=True, depth=True)[0]
+    torch.cuda.synchronize()
+    g = gpu(api, s)
+    assert np.array_equal(b["rgba8"].cpu().numpy(), g["rgba8"])

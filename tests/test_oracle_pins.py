@@ -562,3 +562,48 @@ def test_bulb_trap_on_polar_axis(orc):
             t = orc.trap(s, [0.0, y0, 0.0])
             assert abs(t[0] - m) <= 1e-12 * max(1.0, m)
             assert t[1] == y0 and t[2] == 0.0 and abs(t[3] - y0 * y0) <= 1e-15
+
+
+# ------------------------------------------------------ analytic normal (Sec. 2)
+def test_analytic_normal_reduces_to_complex_derivative(orc):
+    """On span{1, i} with c there too, grad log|z_N| is conj(dz_N/dz_0) z_N in the
+    (x, y) plane (the chain rule D <- 2 z D in complex arithmetic) and 0 along z."""
+    rng = np.random.default_rng(41)
+    s = W.julia_256(8, 8)
+    s["normal_mode"] = "analytic"
+    c = complex(-0.2, 0.6)
+    s["c"] = (c.real, c.imag, 0.0, 0.0)
+    for x, y in rng.uniform(-1.2, 1.2, (300, 2)):
+        z, D = complex(x, y), 1.0 + 0j
+        for _ in range(s["max_iter"]):
+            D = 2 * z * D
+            z = z * z + c
+            if abs(z) ** 2 > s["escape_r2"]:
+                break
+        g = D.conjugate() * z
+        want = np.array([g.real, g.imag, 0.0]) / abs(g)
+        got = orc.normal_scene(s, [x, y, 0.0])
+        assert np.allclose(got, want, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_analytic_normal_matches_fine_central_differences(orc, p):
+    """grad d = (grad G |grad G| - G grad|grad G|) / |grad G|^2 (Sec. 2) tends to
+    grad G / |grad G| as G -> 0: at the hit points (d < eps) the analytic normal
+    mostly agrees with a fine central-difference gradient of the DE; where the
+    orbit has not escaped within the cap the two part ways, so the bar is on the
+    median and on the majority, not on every point."""
+    s = W.julia_256(8, 8)
+    s.update(p=p, escape_r2=256.0 if p == 3 else 16.0, max_iter=12)
+    r = orc.render(W.resized(dict(s, normal_mode="central", normal_h=1e-6), 24, 24), precision="f64")
+    hits = np.flatnonzero((r["flags"] & 1) > 0)
+    assert len(hits) > 50
+    cos = []
+    for idx in hits:
+        ro, rd = orc.camera_ray(W.resized(s, 24, 24), idx % 24, idx // 24)
+        x = ro + r["depth64"][idx] * rd
+        a = orc.normal_scene(dict(s, normal_mode="analytic"), x, rd)
+        b = orc.normal_scene(dict(s, normal_mode="central", normal_h=1e-7), x, rd)
+        cos.append(a @ b)
+    cos = np.array(cos)
+    assert np.median(cos) > 0.99 and np.mean(cos > 0.99) >= 0.6
