@@ -181,6 +181,9 @@ typedef struct {
     int32_t persist_unroll;      /* Julia orbit steps per scheduling round: 1, 2, 4, 8  */
     int32_t single_kernel;       /* fr_render_julia/mandelbulb: 0 nested loops per thread,
                                     1 lane state machine (one DE call site), no queue  */
+    int32_t batch_kernel;        /* fr_render_batch: 0 persistent kernel with the pixel
+                                    queue, 1 one-ray-per-thread kernel over every tile of
+                                    every request in one launch (plain_block threads)  */
 } fr_tuning;
 
 /* Render one quaternion Julia image with the one-ray-per-thread kernel

@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0};
+fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 0};
 
 fr_tuning tuning()
 {
@@ -245,6 +245,7 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
     if (t->refill_threshold < 1 || t->refill_threshold > 32)
         return fail(FR_EINVAL, "refill_threshold outside 1..32");
     if (t->single_kernel != 0 && t->single_kernel != 1) return fail(FR_EINVAL, "single_kernel must be 0 or 1");
+    if (t->batch_kernel != 0 && t->batch_kernel != 1) return fail(FR_EINVAL, "batch_kernel must be 0 or 1");
     std::lock_guard<std::mutex> lk(g_tuning_mu);
     g_tuning = *t;
     return FR_OK;
@@ -330,20 +331,41 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         count = count || q.out.stats != nullptr;
     }
     const fr_tuning tu = tuning();
+    // largest requests first: the small ones then fill in behind the big ones'
+    // slow pixels at the end of the launch (outputs travel with their request)
+    std::vector<int> order((size_t)n_reqs);
+    for (int i = 0; i < n_reqs; i++) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return all[(size_t)a].n_units * all[(size_t)a].spp > all[(size_t)b].n_units * all[(size_t)b].spp;
+    });
     for (int first = 0, chunk = 0; first < n_reqs; first += fr::kMaxReqPerLaunch, chunk++) {
         const int n = std::min(fr::kMaxReqPerLaunch, n_reqs - first);
-        long long units = 0;
-        for (int i = 0; i < n; i++) {
-            A.reqs[i] = all[(size_t)(first + i)];
-            A.reqs[i].unit_begin = units;
-            units += A.reqs[i].n_units;
-        }
         A.n_reqs = n;
-        A.total_units = units;
         A.refill_threshold = tu.refill_threshold;
         A.queue = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 256 * (size_t)chunk);
-        const fr_status st = launched(fr::launch_persist(A, tu.persist_block, tu.persist_ctas_per_sm,
-                                                         tu.persist_unroll, count, (cudaStream_t)stream));
+        fr_status st;
+        if (tu.batch_kernel == 1) {
+            const long long warps = tu.plain_block / 32;
+            long long ctas = 0;
+            for (int i = 0; i < n; i++) {
+                A.reqs[i] = all[(size_t)order[(size_t)(first + i)]];
+                A.reqs[i].unit_begin = ctas;
+                ctas += (A.reqs[i].n_units / 32 + warps - 1) / warps;
+            }
+            A.total_units = ctas;
+            st = launched(fr::launch_batch_plain(A, ctas, tu.plain_block, tu.plain_unroll, count,
+                                                 (cudaStream_t)stream));
+        } else {
+            long long units = 0;
+            for (int i = 0; i < n; i++) {
+                A.reqs[i] = all[(size_t)order[(size_t)(first + i)]];
+                A.reqs[i].unit_begin = units;
+                units += A.reqs[i].n_units;
+            }
+            A.total_units = units;
+            st = launched(fr::launch_persist(A, tu.persist_block, tu.persist_ctas_per_sm, tu.persist_unroll,
+                                             count, (cudaStream_t)stream));
+        }
         if (st != FR_OK) return st;
     }
     return FR_OK;

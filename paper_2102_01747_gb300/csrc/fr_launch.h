@@ -38,6 +38,11 @@ cudaError_t launch_backward(const BwdArgs &A, cudaStream_t s);
 // one-ray-per-thread forward kernel for one request
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s);
 
+// one-ray-per-thread kernel over A.n_reqs requests in one launch; reqs[r].unit_begin
+// holds request r's first CTA, `ctas` the grid size
+cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, int unroll, bool count,
+                               cudaStream_t s);
+
 // lane-state-machine forward kernel without the queue: one pixel per lane, all tiles launched
 cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, cudaStream_t s);
 

@@ -33,6 +33,58 @@ static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Many requests in one launch of the same one-ray-per-thread code: the grid
+// covers every tile of every request, each CTA inside one request (a request's
+// tiles are padded to whole CTAs), so its kind and parameters are uniform and
+// read from the kernel-parameter table.  The hardware block scheduler hands
+// CTAs to SMs as they free up, so the requests' slow pixels overlap instead of
+// each launch waiting for its own.  tile_begin of request r (in CTAs) is kept
+// in reqs[r].unit_begin.
+template <int U, bool COUNT>
+__global__ void __launch_bounds__(256) batch_plain_kernel(const __grid_constant__ BatchArgs A)
+{
+    const int warps = blockDim.x >> 5;
+    const long long cta = blockIdx.x;
+    int lo = 0, hi = A.n_reqs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.reqs[mid].unit_begin <= cta)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const DevReq &R = A.reqs[lo];
+    const long long tile = (cta - R.unit_begin) * warps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int px = (int)(tile % R.tiles_x) * kTileW + (lane & (kTileW - 1));
+    const int py = (int)(tile / R.tiles_x) * kTileH + (lane / kTileW);
+    Counters cnt;
+    if (COUNT)
+        for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
+    if (px < R.width && py < R.height) {
+        if (R.kind == 0)
+            render_pixel<0, U, COUNT>(R, px, py, cnt);
+        else
+            render_pixel<1, U, COUNT>(R, px, py, cnt);
+    }
+    if (COUNT && R.stats) flush_counters(cnt, R.stats);
+}
+
+template <int U, bool COUNT>
+static cudaError_t launch_batch_plain_t(const BatchArgs &A, long long ctas, int block, cudaStream_t s)
+{
+    batch_plain_kernel<U, COUNT><<<(unsigned)ctas, block, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, int unroll, bool count,
+                               cudaStream_t s)
+{
+    if (count) return launch_batch_plain_t<1, true>(A, ctas, block, s);
+    if (unroll == 2) return launch_batch_plain_t<2, false>(A, ctas, block, s);
+    return launch_batch_plain_t<1, false>(A, ctas, block, s);
+}
+
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s)
 {
     if (count) return R.kind == 0 ? launch_plain_t<0, 1, true>(R, block, s)

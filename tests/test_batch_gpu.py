@@ -77,21 +77,29 @@ def test_mixed_batch_equals_plain_and_oracle(api, orc):
 
 
 def test_more_requests_than_one_launch(api):
-    """70 requests -> two launches, each with its own queue head."""
+    """70 requests -> two launches, each with its own queue head; also through the
+    one-ray-per-thread batch kernel."""
     from paper_2102_01747_gb300 import _ffi as F
 
     scenes = [W.julia_256(8 + (i % 5) * 7, 5 + (i % 3) * 4) if i % 2 else
               W.bulb_1080p(i, 9 + (i % 4) * 5, 7 + (i % 6) * 3) for i in range(70)]
     assert F.fr_batch_workspace_bytes(70) == 512
     batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
-    for s, b in zip(scenes, batch):
+    old = tuned(F, batch_kernel=1)
+    try:
+        batch1 = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    finally:
+        F.fr_set_tuning(old)
+    for s, b, b1 in zip(scenes, batch, batch1):
         p = _np([api.render(s, rgba8=True, depth=True)])[0]
         same_or_close(p, b)
+        same_or_close(p, b1)
 
 
 @pytest.mark.parametrize("kw", [
     dict(refill_threshold=1), dict(refill_threshold=32), dict(persist_unroll=1),
-    dict(persist_unroll=4), dict(persist_block=64, persist_ctas_per_sm=1), dict(persist_block=256)])
+    dict(persist_unroll=4), dict(persist_block=64, persist_ctas_per_sm=1), dict(persist_block=256),
+    dict(batch_kernel=1), dict(batch_kernel=1, plain_block=64), dict(batch_kernel=1, plain_block=256)])
 def test_schedule_does_not_change_images(api, kw):
     from paper_2102_01747_gb300 import _ffi as F
 
@@ -122,11 +130,19 @@ def test_batch_counters_equal_plain_counters(api):
     scenes = small_mixed(4, seed=3)
     import torch
 
+    from paper_2102_01747_gb300 import _ffi as F
+
     for s in scenes:
         p = api.render(s, rgba8=False, depth=False, stats=True)
         b = api.render_batch([s], rgba8=False, depth=False, stats=True)[0]
+        old = tuned(F, batch_kernel=1)
+        try:
+            b1 = api.render_batch([s], rgba8=False, depth=False, stats=True)[0]
+        finally:
+            F.fr_set_tuning(old)
         torch.cuda.synchronize()
         assert np.array_equal(p["stats"].cpu().numpy(), b["stats"].cpu().numpy())
+        assert np.array_equal(p["stats"].cpu().numpy(), b1["stats"].cpu().numpy())
 
 
 def test_batch_errors(api):
