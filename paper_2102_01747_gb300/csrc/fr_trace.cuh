@@ -65,6 +65,10 @@ __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd
 // One camera sample: interval, march, normal (the plane's for a cut-face hit:
 // interval starts on the plane and the first DE sample is already inside),
 // optional shadow ray from x + 4 eps n toward the light, Lambert shading.
+// The camera ray and the shadow ray go through the same march loop (two passes
+// of one loop body), so the DE is inlined twice in this function (march and
+// stencil) rather than three times: the Mandelbulb's math-library code is long
+// enough for instruction fetch to stall the warps otherwise.
 template <int KIND, int U, bool COUNT>
 __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float3 rd, float &t_hit,
                                                uint32_t &flags, float3 &xhit, Counters &cnt)
@@ -75,31 +79,38 @@ __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float
     bool fp;
     int steps;
     if (!bounds(R, ro, rd, t0, t1, fp)) return R.bg;
-    if (!march<KIND, U, COUNT>(R, ro, rd, t0, t1, t, steps, cnt, kStatPrimaryDE)) return R.bg;
-    float3 x = along(ro, rd, t);
-    float3 n;
-    uint32_t fl = kFlagHit;
-    if (fp && steps == 1) {
-        n = v3(R.plane_hat);
-        fl |= kFlagFace;
-    } else {
-        n = normal_at<KIND, U, COUNT>(R, x, rd, cnt);
-    }
+    float3 mro = ro, mrd = rd;  // the ray being marched
+    float3 x = v3(0.0f, 0.0f, 0.0f), n = x;
+    uint32_t fl = 0;
     float vis = 1.0f;
-    if (R.shadows) {
-        float3 L = v3(R.light);
-        float3 so = offset_point(x, n, R.shadow_off);
-        float s0, s1, ts;
-        bool sfp;
-        int ss;
-        if (COUNT) cnt.v[kStatShadowRays] += 1;
-        if (bounds(R, so, L, s0, s1, sfp) &&
-            march<KIND, U, COUNT>(R, so, L, s0, s1, ts, ss, cnt, kStatShadowDE)) {
-            vis = 0.0f;
-            fl |= kFlagShadow;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; pass++) {
+        const bool hit = march<KIND, U, COUNT>(R, mro, mrd, t0, t1, t, steps, cnt,
+                                               pass == 0 ? kStatPrimaryDE : kStatShadowDE);
+        if (pass == 1) {
+            if (hit) {
+                vis = 0.0f;
+                fl |= kFlagShadow;
+            }
+            break;
         }
+        if (!hit) return R.bg;
+        x = along(ro, rd, t);
+        t_hit = t;
+        fl = kFlagHit;
+        if (fp && steps == 1) {
+            n = v3(R.plane_hat);
+            fl |= kFlagFace;
+        } else {
+            n = normal_at<KIND, U, COUNT>(R, x, rd, cnt);
+        }
+        if (!R.shadows) break;
+        if (COUNT) cnt.v[kStatShadowRays] += 1;
+        mro = offset_point(x, n, R.shadow_off);
+        mrd = v3(R.light);
+        bool sfp;
+        if (!bounds(R, mro, mrd, t0, t1, sfp)) break;
     }
-    t_hit = t;
     flags = fl;
     xhit = x;
     return shade(R, n, vis);

