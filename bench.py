@@ -6,7 +6,7 @@ and the cut plane z = 0.1 (camera frame 10 of the orbit), rendered through the
 C ABI.  One step = one full frame (every pixel: camera ray, interval, march,
 normal, shadow ray, shading, stores).  Prints one JSON line.
 
-  python bench.py [--steps K] [--warmup W] [--workload NAME] [--path persistent|plain]
+  python bench.py [--steps K] [--warmup W] [--workload NAME] [--path plain|batch]
   python -m torch.distributed.run --nproc-per-node N bench.py --gpus N   (weak scaling:
         every rank renders its own frame of the orbit; no data-path collective)
   python bench.py --impl reference    (the CPU oracle on the host cores, same metric)
@@ -343,18 +343,17 @@ def run_animation(args, torch, api, F, desc, rank, world):
     3k degrees; per-frame device time (CUDA events), median and p95."""
     frames = [W.stress_bulb_4k(k) for k in range(120)]
     out = api.alloc_image(frames[0], rgba8=True, depth=True)
-    ws = api.workspace(1)
     stream = api.current_stream()
     tstream = torch.cuda.current_stream()
-    arrs = [api.request_array([f], [out]) for f in frames]
-    for a in arrs[:args.warmup]:
-        F.check(F.fr_render_batch(a, 1, ws.data_ptr(), ws.numel(), stream))
+    steps = [Renderer(api, F, [f], [out], args.path, stream) for f in frames]
+    for st in steps[:args.warmup]:
+        st()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]
     with ClockSampler(0) as clk:
-        for (a, b), arr in zip(ev, arrs):
+        for (a, b), st in zip(ev, steps):
             a.record(tstream)
-            F.check(F.fr_render_batch(arr, 1, ws.data_ptr(), ws.numel(), stream))
+            st()
             b.record(tstream)
         torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
@@ -366,7 +365,7 @@ def run_animation(args, torch, api, F, desc, rank, world):
         "metric": "ms/frame", "value": statistics.median(ms), "unit": "ms", "n_gpus": world,
         "steps": len(frames), "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": {"workload": desc, "path": "persistent"},
+        "data": "synthetic", "config": {"workload": desc, "path": args.path},
         "p95_ms": srt[int(0.95 * (len(srt) - 1))], "max_ms": srt[-1],
         "per_frame_ms": [round(v, 3) for v in ms],
         "primary_mrays_per_s": sum(rays) / (sum(ms) / 1e3) / 1e6,
@@ -381,8 +380,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bulb_1080p")
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "persistent"],
-                    help="auto: one-ray-per-thread kernel for one request, persistent for batches")
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "batch"],
+                    help="plain: one fr_render_julia/fr_render_mandelbulb call per request; batch: "
+                         "fr_render_batch over all requests (schedule autotuned); auto: plain for one "
+                         "request, batch for several")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the current launch shape")
@@ -416,14 +417,15 @@ def main():
     stream = api.current_stream(dev)
     tstream = torch.cuda.current_stream(dev)
     if args.path == "auto":
-        args.path = "plain" if len(scenes) == 1 else "persistent"
+        # the animation renders its frames one call each
+        args.path = "plain" if len(scenes) == 1 or args.workload == "stress_anim" else "batch"
     if args.workload == "diff_julia":
         return run_gradient(args, torch, api, F, scenes, desc, rank, world)
     if args.workload == "stress_anim":
         return run_animation(args, torch, api, F, desc, rank, world)
 
     tuning = None
-    if args.path == "persistent" and not args.no_autotune:
+    if args.path == "batch" and not args.no_autotune:
         from paper_2102_01747_gb300 import autotune
 
         tuning = autotune.tune(scenes, reps=3)  # untimed search over the launch shape
@@ -444,7 +446,7 @@ def main():
     outs = [api.alloc_image(s, rgba8=True, depth=True) for s in scenes]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    paths = [args.path] + ([] if args.no_compare else [p for p in ("plain", "persistent") if p != args.path])
+    paths = [args.path] + ([] if args.no_compare else [p for p in ("plain", "batch") if p != args.path])
     results = {}
     for path in paths:
         step = Renderer(api, F, scenes, outs, path, stream)
@@ -490,7 +492,8 @@ def main():
 
     if rank != 0:
         return
-    kern = "plain_kernel" if args.path == "plain" else "persist_kernel"
+    kern = ("plain_kernel" if args.path == "plain" else
+            "batch_plain_kernel" if F.fr_get_tuning().batch_kernel == 1 else "persist_kernel")
     res = {
         "metric": "Mrays/s", "value": value, "unit": "Mrays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -535,7 +538,7 @@ def main():
 def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step):
     """Two more views of the same frame: (1) Eq. 1 evaluated without
     transcendental calls (de Moivre powers; same image within the parity bar);
-    (2) eight consecutive frames of the camera orbit in one persistent launch,
+    (2) eight consecutive frames of the camera orbit in one fr_render_batch call,
     where one frame's slowest pixels overlap the other frames' work."""
     out = {}
     alg = [dict(s, algebraic=True) for s in scenes]
@@ -550,12 +553,13 @@ def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step
     frames = [W.bulb_1080p(10 + k) for k in range(8)]
     fouts = [api.alloc_image(f) for f in frames]
     fc = count_frame(api, torch, frames)
-    step = Renderer(api, F, frames, fouts, "persistent", api.current_stream())
+    step = Renderer(api, F, frames, fouts, "batch", api.current_stream())
     for _ in range(args.warmup):
         step()
     times, total, _ = time_steps(torch, step, max(3, args.steps // 4), tstream, flush)
     n = max(3, args.steps // 4)
-    out["eight_frames_in_flight"] = {"path": "persistent", "ms_per_8_frames": total / n * 1e3,
+    out["eight_frames_in_flight"] = {"path": "batch", "batch_kernel": F.fr_get_tuning().batch_kernel,
+                                     "ms_per_8_frames": total / n * 1e3,
                                      "value": (fc[0] + fc[1]) * n / total / 1e6, "unit": "Mrays/s"}
     return out
 

@@ -182,8 +182,9 @@ typedef struct {
     int32_t single_kernel;       /* fr_render_julia/mandelbulb: 0 nested loops per thread,
                                     1 lane state machine (one DE call site), no queue  */
     int32_t batch_kernel;        /* fr_render_batch: 0 persistent kernel with the pixel
-                                    queue, 1 one-ray-per-thread kernel over every tile of
-                                    every request in one launch (plain_block threads)  */
+                                    queue, 1 (default) one-ray-per-thread kernel over
+                                    every tile of every request in one launch
+                                    (plain_block threads)                              */
 } fr_tuning;
 
 /* Render one quaternion Julia image with the one-ray-per-thread kernel
@@ -201,17 +202,24 @@ FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_pla
 /* Device workspace a batch of n_reqs requests needs (bytes, 256-aligned start). */
 FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs);
 
-/* Render n_reqs requests (mixed kinds and sizes) in one persistent launch: CTAs
- * stay resident and each warp pulls pixels from one queue over all requests,
- * refilling idle lanes as rays finish.  The request table travels in the
- * kernel's parameters (staged into shared memory by every CTA), so the call is
- * a memset of the queue heads plus one kernel launch per 64 requests, with no
- * host synchronisation and no copy: it can be captured into a CUDA graph and
- * replayed.  `workspace` (device, >= fr_batch_workspace_bytes(n_reqs) bytes,
- * 256-byte aligned) holds the queue heads and is overwritten; two batches in
- * flight at once need two workspaces.  reqs is host memory.
- * 1 <= n_reqs <= 4096.  Errors: FR_EINVAL, FR_ENOMEM (workspace too small),
- * FR_ECUDA. */
+/* Render n_reqs requests (mixed kinds and sizes) with one kernel launch per 64
+ * requests (largest first).  Two schedules, picked by fr_tuning.batch_kernel:
+ *   1 (default)  one-ray-per-thread kernel over every tile of every request:
+ *                each CTA belongs to one request and the hardware block
+ *                scheduler hands CTAs to SMs as they free up, so the slow
+ *                pixels of different requests overlap;
+ *   0            persistent CTAs, each warp pulling pixels from one queue over
+ *                all requests and refilling idle lanes as rays finish.
+ * Images are the same bit for bit either way (and equal fr_render_julia /
+ * fr_render_mandelbulb of each request).  The request table travels in the
+ * kernel's parameters, so the call is at most a memset of the queue heads plus
+ * one launch per 64 requests, with no host synchronisation and no copy: it can
+ * be captured into a CUDA graph and replayed.  `workspace` (device,
+ * >= fr_batch_workspace_bytes(n_reqs) bytes, 256-byte aligned) holds the
+ * queue heads and is overwritten; two batches in flight at once need two
+ * workspaces.  reqs is host memory.  1 <= n_reqs <= 4096.  Errors: FR_EINVAL
+ * (also when one launch's 64 requests would need more than 2^31 - 1 CTAs),
+ * FR_ENOMEM (workspace too small), FR_ECUDA. */
 FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *workspace,
                                  size_t ws_bytes, void *stream);
 

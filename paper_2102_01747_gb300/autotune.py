@@ -1,12 +1,15 @@
-"""Autotuner for the persistent kernel's launch shape (fr_tuning).
+"""Autotuner for the batched path's schedule and launch shape (fr_tuning).
 
-The knobs are the ones the batched path is sensitive to:
-  persist_block      threads per CTA (64, 128, 256)
+The knobs are the ones fr_render_batch is sensitive to:
+  batch_kernel       1 one-ray-per-thread kernel over all tiles, 0 persistent kernel
+  plain_block        threads per CTA of the one-ray-per-thread batch kernel
+  persist_block      threads per CTA of the persistent kernel (64, 128, 256)
   refill_threshold   idle lanes that trigger a warp refill (the compaction interval)
   persist_unroll     Julia orbit steps per scheduling round (the unroll depth)
 The search is coordinate descent from the current setting: each knob in turn is
 swept with the others fixed, each candidate timed with CUDA events (median of a
-few launches of fr_render_batch on the caller's scenes), and the best kept.
+few launches of fr_render_batch on the caller's scenes), and the best kept.  A
+knob of the schedule not in use is skipped.
 Results are cached in a JSON file keyed by GPU name and workload key, so a
 later process applies them without searching again.
 """
@@ -21,6 +24,8 @@ from . import _ffi as F
 from . import api
 
 SPACE = {
+    "batch_kernel": (1, 0),
+    "plain_block": (64, 128, 256),
     "persist_block": (64, 128, 256),
     "refill_threshold": (1, 2, 4, 8, 16),
     "persist_unroll": (2, 4, 8),
@@ -59,6 +64,18 @@ def _time_batch(scenes, outs, ws, reps: int) -> float:
     return times[len(times) // 2]
 
 
+PERSIST_KNOBS = ("persist_block", "persist_ctas_per_sm", "refill_threshold", "persist_unroll")
+
+
+def _in_use(knob: str, cfg: dict) -> bool:
+    """Whether `knob` changes what fr_render_batch launches under `cfg`."""
+    if knob in PERSIST_KNOBS:
+        return cfg.get("batch_kernel", 0) == 0
+    if knob == "plain_block":
+        return cfg.get("batch_kernel", 0) == 1
+    return True
+
+
 def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=None) -> dict:
     """Coordinate descent over `space`; returns {"config": ..., "ms": ..., "trials": [...]}
     and leaves the best configuration applied."""
@@ -70,6 +87,8 @@ def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=
     trials = [dict(best, ms=best_ms)]
     for _ in range(passes):
         for knob, values in space.items():
+            if not _in_use(knob, best):
+                continue
             for v in values:
                 if v == best[knob]:
                     continue

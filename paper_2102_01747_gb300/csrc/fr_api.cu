@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 0};
+fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 1};
 
 fr_tuning tuning()
 {
@@ -338,6 +338,16 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return all[(size_t)a].n_units * all[(size_t)a].spp > all[(size_t)b].n_units * all[(size_t)b].spp;
     });
+    const long long warps_per_cta = tu.plain_block / 32;
+    auto ctas_of = [&](const fr::DevReq &R) { return (R.n_units / 32 + warps_per_cta - 1) / warps_per_cta; };
+    if (tu.batch_kernel == 1)  // the grid of each launch must fit the 2^31 - 1 CTA limit
+        for (int first = 0; first < n_reqs; first += fr::kMaxReqPerLaunch) {
+            long long ctas = 0;
+            for (int i = first; i < std::min(n_reqs, first + fr::kMaxReqPerLaunch); i++)
+                ctas += ctas_of(all[(size_t)order[(size_t)i]]);
+            if (ctas > 2147483647LL)
+                return fail(FR_EINVAL, "one launch of this batch would need %lld CTAs (at most 2^31 - 1)", ctas);
+        }
     for (int first = 0, chunk = 0; first < n_reqs; first += fr::kMaxReqPerLaunch, chunk++) {
         const int n = std::min(fr::kMaxReqPerLaunch, n_reqs - first);
         A.n_reqs = n;
@@ -345,12 +355,11 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         A.queue = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 256 * (size_t)chunk);
         fr_status st;
         if (tu.batch_kernel == 1) {
-            const long long warps = tu.plain_block / 32;
             long long ctas = 0;
             for (int i = 0; i < n; i++) {
                 A.reqs[i] = all[(size_t)order[(size_t)(first + i)]];
                 A.reqs[i].unit_begin = ctas;
-                ctas += (A.reqs[i].n_units / 32 + warps - 1) / warps;
+                ctas += ctas_of(A.reqs[i]);
             }
             A.total_units = ctas;
             st = launched(fr::launch_batch_plain(A, ctas, tu.plain_block, tu.plain_unroll, count,

@@ -162,3 +162,40 @@ def test_tuning_roundtrip_and_checks(F):
     assert F.fr_set_tuning(good) == F.FR_OK
     assert F.fr_get_tuning().plain_block == 64
     assert F.fr_set_tuning(F.fr_tuning(*old)) == F.FR_OK
+
+
+def test_batch_grid_limit_refused_before_launch(F):
+    """64 requests of 46000 x 46000 pixels with 32-thread CTAs need 4.3e9 CTAs in
+    one launch of the one-ray-per-thread batch kernel: refused on the host.  The
+    outputs are placeholder addresses that must never reach a kernel, so this
+    runs only where there is no GPU at all."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("placeholder output addresses: host-only check")
+    s = W.julia_256(46000, 46000)
+    req = F.fr_request()
+    req.kind = F.FR_KIND_JULIA
+    req.julia, req.plane, req.camera, req.light = _structs(s)
+    req.out.rgba8 = 1 << 20  # placeholder, 256-byte aligned, never dereferenced
+    arr = (F.fr_request * 64)(*([req] * 64))
+    old = F.fr_get_tuning()
+    t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+    t.batch_kernel, t.plain_block = 1, 32
+    assert F.fr_set_tuning(t) == F.FR_OK
+    try:
+        st = F.fr_render_batch(arr, 64, 1 << 21, F.fr_batch_workspace_bytes(64), None)
+        msg = F.fr_last_error()
+    finally:
+        F.fr_set_tuning(F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_]))
+    assert st == F.FR_EINVAL and "CTAs" in msg, msg
+
+
+def test_autotune_skips_knobs_of_the_other_schedule():
+    from paper_2102_01747_gb300 import autotune
+
+    assert autotune._in_use("batch_kernel", {"batch_kernel": 1})
+    assert autotune._in_use("plain_block", {"batch_kernel": 1})
+    assert not autotune._in_use("refill_threshold", {"batch_kernel": 1})
+    assert autotune._in_use("persist_unroll", {"batch_kernel": 0})
+    assert not autotune._in_use("plain_block", {"batch_kernel": 0})

@@ -1,6 +1,8 @@
-"""Persistent batched kernel (fr_render_batch) on the GPU: per-request outputs
-equal the one-ray-per-thread kernel's, every request matches the oracle, and
-the batch bookkeeping (several launches, workspace, counters) holds."""
+"""Batched rendering (fr_render_batch) on the GPU, through both of its
+schedules (batch_kernel 1: one-ray-per-thread kernel over every tile of every
+request; batch_kernel 0: persistent kernel with the pixel queue): per-request
+outputs equal the single-request kernel's, every request matches the oracle,
+and the batch bookkeeping (several launches, workspace, counters) holds."""
 import os
 
 import numpy as np
@@ -58,14 +60,31 @@ def tuned(F, **kw):
     return F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
 
 
-def test_single_request_equals_plain(api):
+@pytest.fixture(params=[1, 0], ids=["batch_kernel1", "batch_kernel0"])
+def schedule(request):
+    """Run the test under each batch schedule, then restore the tuning."""
+    from paper_2102_01747_gb300 import _ffi as F
+
+    F.load()
+    old = tuned(F, batch_kernel=request.param)
+    yield request.param
+    F.fr_set_tuning(old)
+
+
+def test_default_schedule_is_the_batch_kernel(api):
+    from paper_2102_01747_gb300 import _ffi as F
+
+    assert F.fr_get_tuning().batch_kernel == 1
+
+
+def test_single_request_equals_plain(api, schedule):
     for scene in (W.bulb_1080p(10, 320, 180), W.julia_256(200, 150)):
         plain = _np([api.render(scene, rgba8=True, depth=True, saved=True)])[0]
         batch = _np(api.render_batch([scene], rgba8=True, depth=True, saved=True))[0]
         same_or_close(plain, batch)
 
 
-def test_mixed_batch_equals_plain_and_oracle(api, orc):
+def test_mixed_batch_equals_plain_and_oracle(api, orc, schedule):
     scenes = small_mixed()
     batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
     for s, b in zip(scenes, batch):
@@ -84,7 +103,11 @@ def test_more_requests_than_one_launch(api):
     scenes = [W.julia_256(8 + (i % 5) * 7, 5 + (i % 3) * 4) if i % 2 else
               W.bulb_1080p(i, 9 + (i % 4) * 5, 7 + (i % 6) * 3) for i in range(70)]
     assert F.fr_batch_workspace_bytes(70) == 512
-    batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    old = tuned(F, batch_kernel=0)
+    try:
+        batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    finally:
+        F.fr_set_tuning(old)
     old = tuned(F, batch_kernel=1)
     try:
         batch1 = _np(api.render_batch(scenes, rgba8=True, depth=True))
@@ -97,9 +120,11 @@ def test_more_requests_than_one_launch(api):
 
 
 @pytest.mark.parametrize("kw", [
-    dict(refill_threshold=1), dict(refill_threshold=32), dict(persist_unroll=1),
-    dict(persist_unroll=4), dict(persist_block=64, persist_ctas_per_sm=1), dict(persist_block=256),
-    dict(batch_kernel=1), dict(batch_kernel=1, plain_block=64), dict(batch_kernel=1, plain_block=256)])
+    dict(batch_kernel=0, refill_threshold=1), dict(batch_kernel=0, refill_threshold=32),
+    dict(batch_kernel=0, persist_unroll=1), dict(batch_kernel=0, persist_unroll=4),
+    dict(batch_kernel=0, persist_block=64, persist_ctas_per_sm=1), dict(batch_kernel=0, persist_block=256),
+    dict(batch_kernel=1), dict(batch_kernel=1, plain_block=64), dict(batch_kernel=1, plain_block=256),
+    dict(batch_kernel=1, plain_unroll=2)])
 def test_schedule_does_not_change_images(api, kw):
     from paper_2102_01747_gb300 import _ffi as F
 
@@ -114,7 +139,7 @@ def test_schedule_does_not_change_images(api, kw):
         same_or_close(a, b)
 
 
-def test_jittered_and_shadowed_batch(api, orc):
+def test_jittered_and_shadowed_batch(api, orc, schedule):
     s = W.bulb_1080p(30, 64, 48)
     s["camera"]["spp"] = 3
     s["camera"]["seed"] = 11
@@ -134,7 +159,11 @@ def test_batch_counters_equal_plain_counters(api):
 
     for s in scenes:
         p = api.render(s, rgba8=False, depth=False, stats=True)
-        b = api.render_batch([s], rgba8=False, depth=False, stats=True)[0]
+        old = tuned(F, batch_kernel=0)
+        try:
+            b = api.render_batch([s], rgba8=False, depth=False, stats=True)[0]
+        finally:
+            F.fr_set_tuning(old)
         old = tuned(F, batch_kernel=1)
         try:
             b1 = api.render_batch([s], rgba8=False, depth=False, stats=True)[0]
@@ -160,3 +189,24 @@ def test_batch_errors(api):
     arr[1].kind = 9
     assert F.fr_render_batch(arr, 3, ws.data_ptr(), 1024, None) == F.FR_EINVAL
     assert "request 1" in F.fr_last_error()
+
+
+def test_autotune_keeps_images_and_applies_its_choice(api):
+    """The autotuner's search (both schedules, their launch shapes) leaves its best
+    configuration applied, and the images under it equal the plain kernel's."""
+    from paper_2102_01747_gb300 import _ffi as F
+    from paper_2102_01747_gb300 import autotune
+
+    scenes = small_mixed(4, seed=21)
+    old = tuned(F)
+    try:
+        res = autotune.tune(scenes, reps=1, space={"batch_kernel": (1, 0), "plain_block": (64, 128),
+                                                   "refill_threshold": (4, 16)})
+        cur = autotune.current()
+        assert all(cur[k] == v for k, v in res["config"].items())
+        assert len(res["trials"]) >= 2 and res["ms"] == min(t["ms"] for t in res["trials"])
+        got = _np(api.render_batch(scenes, rgba8=True, depth=True))
+    finally:
+        F.fr_set_tuning(old)
+    for s, b in zip(scenes, got):
+        same_or_close(_np([api.render(s, rgba8=True, depth=True)])[0], b)
