@@ -140,7 +140,7 @@ def _oracle_rays(oracle, scenes, samples, threads):
     rays = 0
     for s, px in zip(scenes, samples):
         r = oracle.render(s, pixels=px, precision="f32", threads=threads)
-        rays += len(px) * s["camera"]["spp"] + int(r["stats"][:, 4].sum())
+        rays += len(px) * s["camera"]["spp"] + int(r["stats"][:, 4].sum()) + int(r["stats"][:, 6].sum())
     return rays
 
 

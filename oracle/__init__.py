@@ -27,6 +27,7 @@ SOURCES = ["fr_oracle.c", "fr_oracle_body.inc", "fr_oracle_grad.inc", "fr_oracle
 
 JULIA, BULB = 0, 1
 NORMAL_TETRA, NORMAL_CENTRAL, NORMAL_ANALYTIC = 0, 1, 2
+SHADE_LAMBERT, SHADE_PHONG = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +77,10 @@ class OrcScene(ctypes.Structure):
         ("k_diffuse", ctypes.c_double),
         ("shadows", ctypes.c_int),
         ("background", ctypes.c_double * 4),
+        ("shading", ctypes.c_int),
+        ("k_specular", ctypes.c_double),
+        ("shininess", ctypes.c_double),
+        ("reflect_coef", ctypes.c_double),
     ]
 
 
@@ -127,6 +132,7 @@ def lib():
         L.orc_march_field_d.restype = i
         L.orc_normal_field_d.argtypes = [i, pd, pd, i, d, pd, pd]
         L.orc_shade_d.argtypes = [P(OrcScene), pd, d, pd]
+        L.orc_shade_phong_d.argtypes = [P(OrcScene), pd, pd, d, pd, pd]
         L.orc_julia_grad_d.argtypes = [P(OrcScene), pd, pd, ctypes.c_void_p, pd, i]
         L.orc_julia_grad_d.restype = i
         _lib = L
@@ -177,6 +183,10 @@ def scene_struct(scene: dict) -> OrcScene:
     s.k_diffuse = float(li["k_diffuse"])
     s.shadows = 1 if li["shadows"] else 0
     s.background[:] = [float(v) for v in li["background"]]
+    s.shading = {"lambert": SHADE_LAMBERT, "phong": SHADE_PHONG}[li.get("shading", "lambert")]
+    s.k_specular = float(li.get("k_specular", 0.0))
+    s.shininess = float(li.get("shininess", 1.0))
+    s.reflect_coef = float(li.get("reflect_coef", 0.0))
     return s
 
 
@@ -185,8 +195,9 @@ def render(scene: dict, pixels=None, precision: str = "f32", threads: int = 1) -
 
     Returns numpy arrays: rgba (n,4) float32 mean colour, rgba8 (n,) uint32,
     depth (n,) float32 (+inf on a miss), flags (n,) int32 (1 hit, 2 cut face,
-    4 shadowed), stats (n,5) int64 (primary DE calls, normal DE calls, shadow DE
-    calls, orbit iterations, shadow rays), trap (n,4) float32 orbit-trap colour
+    4 shadowed), stats (n,7) int64 (primary DE calls, normal DE calls, shadow DE
+    calls, orbit iterations, shadow rays, reflection DE calls, reflection
+    rays), trap (n,4) float32 orbit-trap colour
     parameters at the nearest hit, and for f64 also rgba64 / depth64."""
     L = lib()
     s = scene_struct(scene)
@@ -201,7 +212,7 @@ def render(scene: dict, pixels=None, precision: str = "f32", threads: int = 1) -
         "rgba8": np.zeros(n, np.uint32),
         "depth": np.zeros(n, np.float32),
         "flags": np.zeros(n, np.int32),
-        "stats": np.zeros((n, 5), np.int64),
+        "stats": np.zeros((n, 7), np.int64),
         "trap": np.zeros((n, 4), np.float32),
     }
     out = OrcOutputs(res["rgba"].ctypes.data, res["rgba8"].ctypes.data, res["depth"].ctypes.data,
@@ -322,6 +333,16 @@ def shade(scene, n, vis=1.0):
     n = _arr(n)
     o = np.zeros(4)
     lib().orc_shade_d(ctypes.byref(s), _ptr(n), float(vis), _ptr(o))
+    return o
+
+
+def shade_phong(scene, n, rd, vis=1.0, refl=(0.0, 0.0, 0.0)):
+    """Phong colour of a hit with normal n seen along rd (visibility vis), plus
+    reflect_coef * Fresnel-Schlick * refl (the colour along the mirror ray)."""
+    s = scene_struct(scene)
+    n, rd, refl = _arr(n), _arr(rd), _arr(refl)
+    o = np.zeros(4)
+    lib().orc_shade_phong_d(ctypes.byref(s), _ptr(n), _ptr(rd), float(vis), _ptr(refl), _ptr(o))
     return o
 
 

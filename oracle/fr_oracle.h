@@ -23,6 +23,7 @@
  *   interval clip by bounding sphere and cutting plane      Sec. 3.1 (text before that listing)
  *   tetrahedral gradient                                    Eq. 5 and Listing "Normal calculation"
  *   hit -> normal -> shade                                  Listings "JuliaDistance", "Closest-hit shader"
+ *   Phong + Fresnel-Schlick reflection bounce               closest-hit listing of Sec. 3.1
  */
 #ifndef FR_ORACLE_H
 #define FR_ORACLE_H
@@ -35,6 +36,7 @@ extern "C" {
 
 enum { ORC_JULIA = 0, ORC_BULB = 1 };
 enum { ORC_NORMAL_TETRA = 0, ORC_NORMAL_CENTRAL = 1, ORC_NORMAL_ANALYTIC = 2 };
+enum { ORC_SHADE_LAMBERT = 0, ORC_SHADE_PHONG = 1 };
 
 /* One render request.  All reals are doubles; the float build rounds them. */
 typedef struct {
@@ -70,6 +72,13 @@ typedef struct {
     double k_ambient, k_diffuse;
     int shadows;
     double background[4];
+    /* closest-hit model: ORC_SHADE_LAMBERT, or ORC_SHADE_PHONG = Phong lighting
+     * plus one reflection bounce weighted by Fresnel-Schlick (the paper's
+     * closest-hit listing for the Julia set) */
+    int shading;
+    double k_specular;        /* white specular weight */
+    double shininess;         /* Phong exponent */
+    double reflect_coef;      /* weight of the reflected colour (0.1 in the listing) */
 } orc_scene;
 
 /* Per-pixel outputs.  Any pointer may be NULL. */
@@ -78,8 +87,9 @@ typedef struct {
     uint32_t *rgba8;          /* n, r | g<<8 | b<<16 | a<<24              */
     float *depth;             /* n, min hit t over samples, +inf on miss  */
     int32_t *flags;           /* n, OR over samples: 1 hit, 2 cut face, 4 shadowed */
-    int64_t *stats;           /* n x 5: primary DE calls, normal DE calls, shadow DE calls,
-                                 orbit iterations, shadow rays             */
+    int64_t *stats;           /* n x 7: primary DE calls, normal DE calls, shadow DE calls,
+                                 orbit iterations, shadow rays, reflection DE calls,
+                                 reflection rays                           */
     double *rgba64;           /* n x 4, same as rgba at the render precision (double build) */
     double *depth64;          /* n */
     float *trap;              /* n x 4, orbit-trap colour parameters at the nearest hit
@@ -127,6 +137,10 @@ void orc_normal_field_d(int kind, const double *prm, const double p[3], int mode
                         const double rd[3], double n_out[3]);
 /* Lambert closed-hit shading of one sample and the 8-bit quantiser */
 void orc_shade_d(const orc_scene *s, const double n[3], double vis, double rgba_out[4]);
+/* Phong closest-hit colour of one sample seen along rd, with visibility vis,
+ * plus reflect_coef * Fresnel-Schlick(albedo) * refl_rgb (the reflected colour) */
+void orc_shade_phong_d(const orc_scene *s, const double n[3], const double rd[3], double vis,
+                       const double refl_rgb[3], double rgba_out[4]);
 /* unit normal at a point by the scene's normal mode (tetrahedral, central, or
  * -- Julia only -- analytic); rd is the fallback direction's ray */
 void orc_normal_scene_d(const orc_scene *s, const double p[3], const double rd[3], double n[3]);

@@ -12,7 +12,9 @@ can be fed from it.  A scene is a plain dict:
      "max_step": 0.2, "normal_mode": "central" | "tetra", "normal_h": 1e-4,
      "plane": None | {"n": (3,), "o": float},     # keep dot(n, x) <= o
      "camera": {"eye", "target", "up", "fov_y_deg", "width", "height", "spp", "seed"},
-     "light": {"dir", "albedo", "k_ambient", "k_diffuse", "shadows", "background"}}
+     "light": {"dir", "albedo", "k_ambient", "k_diffuse", "shadows", "background",
+               # optional closest-hit model (default "lambert"):
+               "shading": "lambert" | "phong", "k_specular", "shininess", "reflect_coef"}}
 
 The fixed workloads are the ones the renderer is measured on:
   julia_256           quaternion Julia q^2 + c, c = (-0.2, 0.6, 0.2, 0), 256x256
@@ -23,6 +25,8 @@ The fixed workloads are the ones the renderer is measured on:
   diff_julia          512x512 Julia with a hidden c* for gradient recovery
   stress_bulb_4k      Mandelbulb n = 8, 3840x2160, 4 jittered samples, iteration cap 4..20
   stress_julia_4k     Julia (julia_256 parameters) at 3840x2160 with shadow rays
+  phong(scene)        the same scene lit by Phong + one Fresnel-weighted reflection
+                      bounce (the paper's closest-hit model) over a sky-blue background
 """
 from __future__ import annotations
 
@@ -177,6 +181,25 @@ def stress_julia_4k(width: int = 3840, height: int = 2160) -> dict:
     """Quaternion Julia (julia_256 parameters) at 3840x2160 with one shadow ray per hit."""
     s = julia_256(width, height)
     s["light"]["shadows"] = True
+    return s
+
+
+PHONG_LIGHT = {
+    "shading": "phong",
+    "k_specular": 0.5,
+    "shininess": 32.0,
+    "reflect_coef": 0.1,  # the closest-hit listing's reflection weight
+    "background": (0.25, 0.35, 0.5, 1.0),
+}
+
+
+def phong(scene: dict, **light) -> dict:
+    """A copy of `scene` shaded with the Phong + reflection model (white highlight
+    k_specular 0.5, exponent 32, reflection weight 0.1, sky-blue background);
+    keyword arguments override those light fields."""
+    s = copy.deepcopy(scene)
+    s["light"].update(PHONG_LIGHT)
+    s["light"].update(light)
     return s
 
 
