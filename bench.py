@@ -62,6 +62,10 @@ def workload(name: str, rank: int = 0):
     if name == "batch_small":
         sc = W.batch_mixed(W.BASE_SEED + rank, 64, 5.0, 8.0)
         return sc, "64 mixed requests, sides 32..256 (small case)"
+    if name == "bulb_1080p_phong":
+        return [W.phong(W.bulb_1080p(10 + rank))], (
+            "Mandelbulb n=8 1920x1080 (bulb_1080p scene) with Phong lighting and one Fresnel-weighted "
+            "mirror ray per hit, frame %d" % (10 + rank))
     if name == "stress_bulb_4k":
         return [W.stress_bulb_4k(60 + rank)], "Mandelbulb n=8 3840x2160 4 spp, iteration cap 12 (frame 60)"
     if name == "stress_julia_4k":
@@ -270,7 +274,9 @@ def max_over_ranks(torch, dist, seconds: float, device) -> float:
 
 def count_frame(api, torch, scenes):
     """Counting-kernel pass (untimed): summed FR_STAT_* counters of all scenes."""
-    tot = [0] * 6
+    from paper_2102_01747_gb300 import _ffi as F
+
+    tot = [0] * F.FR_NSTATS
     for s in scenes:
         c = api.render(s, rgba8=False, depth=False, stats=True)
         torch.cuda.synchronize()
@@ -438,8 +444,8 @@ def main():
             per_scene_iters.append(count_frame(api, torch, [s])[5])
     else:
         per_scene_iters = [counts[5]]
-    rays_per_step = counts[0] + counts[1]
-    de_per_step = counts[2] + counts[3] + counts[4]
+    rays_per_step = counts[0] + counts[1] + counts[6]  # camera, shadow and mirror rays
+    de_per_step = counts[2] + counts[3] + counts[4] + counts[7]
     iters_per_step = counts[5]
     flops_per_step = flops_of(scenes, per_scene_iters)
 
@@ -506,7 +512,7 @@ def main():
         "de_evals_per_s": de_per_step * args.steps * world / total_s,
         "orbit_iters_per_s": iters_per_step * args.steps * world / total_s,
         "per_step": {"rays": rays_per_step, "primary_rays": counts[0], "shadow_rays": counts[1],
-                     "de_calls": de_per_step, "orbit_iters": iters_per_step},
+                     "mirror_rays": counts[6], "de_calls": de_per_step, "orbit_iters": iters_per_step},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, args.path)),
                      "kernel": kern,
@@ -548,7 +554,7 @@ def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step
         step()
     times, total, _ = time_steps(torch, step, args.steps, tstream, flush)
     out["algebraic_power"] = {"path": "plain", "ms_per_frame": total / args.steps * 1e3,
-                              "value": (counts[0] + counts[1]) * args.steps / total / 1e6,
+                              "value": (counts[0] + counts[1] + counts[6]) * args.steps / total / 1e6,
                               "unit": "Mrays/s", "orbit_iters": counts[5]}
     frames = [W.bulb_1080p(10 + k) for k in range(8)]
     fouts = [api.alloc_image(f) for f in frames]
@@ -560,7 +566,7 @@ def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step
     n = max(3, args.steps // 4)
     out["eight_frames_in_flight"] = {"path": "batch", "batch_kernel": F.fr_get_tuning().batch_kernel,
                                      "ms_per_8_frames": total / n * 1e3,
-                                     "value": (fc[0] + fc[1]) * n / total / 1e6, "unit": "Mrays/s"}
+                                     "value": (fc[0] + fc[1] + fc[6]) * n / total / 1e6, "unit": "Mrays/s"}
     return out
 
 

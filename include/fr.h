@@ -63,6 +63,7 @@ typedef enum {
 
 enum { FR_KIND_JULIA = 0, FR_KIND_BULB = 1 };
 enum { FR_NORMAL_TETRA = 0, FR_NORMAL_CENTRAL = 1, FR_NORMAL_ANALYTIC = 2 };
+enum { FR_SHADE_LAMBERT = 0, FR_SHADE_PHONG = 1 };
 
 /* indices into fr_image.stats */
 enum {
@@ -72,7 +73,9 @@ enum {
     FR_STAT_NORMAL_DE = 3,     /* distance-estimator calls of the normal stencils     */
     FR_STAT_SHADOW_DE = 4,     /* distance-estimator calls of shadow-ray marches      */
     FR_STAT_ORBIT_ITERS = 5,   /* orbit loop trips summed over all DE calls           */
-    FR_NSTATS = 6
+    FR_STAT_REFLECT_RAYS = 6,  /* reflection rays cast (one per hit, Phong shading)   */
+    FR_STAT_REFLECT_DE = 7,    /* distance-estimator calls of reflection-ray marches  */
+    FR_NSTATS = 8
 };
 
 /* Pinhole camera.  Forward = target - eye, right = forward x up, vertical field
@@ -85,15 +88,36 @@ typedef struct {
     uint32_t seed;           /* jitter seed (used when spp > 1)        */
 } fr_camera;
 
-/* Directional light with Lambert shading:
+/* Directional light and the closest-hit model.
+ * FR_SHADE_LAMBERT:
  *   hit:  rgb = albedo * (k_ambient + k_diffuse * max(0, n . L) * visible), a = 1
- *   miss: rgba = background */
+ * FR_SHADE_PHONG (the closest-hit shader of Sec. 3.1: Phong lighting plus a
+ * reflection ray weighted by the Fresnel-Schlick reflectance; its helpers are
+ * not listed, so the model is stated here):
+ *   phong(n, d, vis) = albedo * (k_ambient + k_diffuse * max(0, n . L) * vis)
+ *                      + k_specular * vis * max(0, r . (-d))^shininess,
+ *                      r = 2 (n . L) n - L, no highlight where n . L <= 0
+ *   hit:  rgb = phong(n, rd, visible) + reflect_coef * F * refl, a = 1, where
+ *         F = albedo + (1 - albedo) (1 - max(0, -n . rd))^5 per channel, and
+ *         refl = phong(n2, rr, 1) at the first hit of the mirror ray
+ *         rr = rd - 2 (n . rd) n from x + 4 eps n (normal n2 by the request's
+ *         normal scheme, no shadow ray, no further bounce), background rgb on
+ *         a miss
+ *   miss: rgba = background
+ * The Phong model runs on the one-ray-per-thread kernels (fr_render_julia,
+ * fr_render_mandelbulb with single_kernel 0, fr_render_batch with
+ * batch_kernel 1); the lane kernels refuse it with FR_ENOTIMPL and the adjoint
+ * with FR_EINVAL. */
 typedef struct {
     float dir[3];            /* toward the light; normalised here, must be non-zero */
     float albedo[3];
     float k_ambient, k_diffuse;
     int32_t shadows;         /* 1: one shadow ray per hit, start x + 4 eps n      */
     float background[4];
+    int32_t shading;         /* FR_SHADE_LAMBERT or FR_SHADE_PHONG                 */
+    float k_specular;        /* >= 0 (Phong)                                       */
+    float shininess;         /* 1..4096 (Phong)                                    */
+    float reflect_coef;      /* 0..1; the listing uses 0.1 (Phong)                 */
 } fr_light;
 
 /* Cutting plane (Sec. 3.1, Fig. 1): points with dot(n, x) > offset are removed.
@@ -253,7 +277,8 @@ FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, 
  *            pixels ignored)
  *   grad     11 floats (device), ADDED to: dc[4], dplane_n[3], dplane_offset,
  *            dlight_dir[3]
- * Errors: FR_EINVAL (spp != 1, NULL buffers, bad parameters), FR_ECUDA. */
+ * Errors: FR_EINVAL (spp != 1, Phong shading, NULL buffers, bad parameters),
+ * FR_ECUDA. */
 FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,
                                     const fr_camera *camera, const fr_light *light,
                                     const float *saved, const float *d_rgba, const float *d_depth,

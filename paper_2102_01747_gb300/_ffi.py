@@ -16,8 +16,10 @@ c_int32, c_uint32, c_float, c_void_p = ctypes.c_int32, ctypes.c_uint32, ctypes.c
 FR_OK, FR_EINVAL, FR_ECUDA, FR_ETIMEOUT, FR_ENOMEM, FR_ENOTIMPL = range(6)
 FR_KIND_JULIA, FR_KIND_BULB = 0, 1
 FR_NORMAL_TETRA, FR_NORMAL_CENTRAL, FR_NORMAL_ANALYTIC = 0, 1, 2
+FR_SHADE_LAMBERT, FR_SHADE_PHONG = 0, 1
 (FR_STAT_PRIMARY_RAYS, FR_STAT_SHADOW_RAYS, FR_STAT_PRIMARY_DE, FR_STAT_NORMAL_DE,
- FR_STAT_SHADOW_DE, FR_STAT_ORBIT_ITERS, FR_NSTATS) = range(7)
+ FR_STAT_SHADOW_DE, FR_STAT_ORBIT_ITERS, FR_STAT_REFLECT_RAYS, FR_STAT_REFLECT_DE,
+ FR_NSTATS) = range(9)
 STATUS_NAMES = {0: "FR_OK", 1: "FR_EINVAL", 2: "FR_ECUDA", 3: "FR_ETIMEOUT", 4: "FR_ENOMEM",
                 5: "FR_ENOTIMPL"}
 
@@ -30,7 +32,9 @@ class fr_camera(ctypes.Structure):
 
 class fr_light(ctypes.Structure):
     _fields_ = [("dir", c_float * 3), ("albedo", c_float * 3), ("k_ambient", c_float),
-                ("k_diffuse", c_float), ("shadows", c_int32), ("background", c_float * 4)]
+                ("k_diffuse", c_float), ("shadows", c_int32), ("background", c_float * 4),
+                ("shading", c_int32), ("k_specular", c_float), ("shininess", c_float),
+                ("reflect_coef", c_float)]
 
 
 class fr_plane(ctypes.Structure):

@@ -75,6 +75,10 @@ def light_struct(scene: dict) -> F.fr_light:
     L.k_ambient, L.k_diffuse = float(li["k_ambient"]), float(li["k_diffuse"])
     L.shadows = 1 if li["shadows"] else 0
     L.background = _f(li["background"], 4)
+    L.shading = {"lambert": F.FR_SHADE_LAMBERT, "phong": F.FR_SHADE_PHONG}[li.get("shading", "lambert")]
+    L.k_specular = float(li.get("k_specular", 0.0))
+    L.shininess = float(li.get("shininess", 1.0))
+    L.reflect_coef = float(li.get("reflect_coef", 0.0))
     return L
 
 
@@ -82,7 +86,7 @@ def alloc_image(scene: dict, device="cuda", rgba8=True, rgba=False, depth=True, 
                 stats=False, trap=False) -> dict:
     """Output tensors for one scene: rgba8 (H, W) int32 holding the packed
     uint32, rgba (H, W, 4) float32, depth (H, W) float32, saved (H, W, 4)
-    float32, stats (6,) int64 (zeroed), trap (H, W, 4) float32."""
+    float32, stats (FR_NSTATS,) int64 (zeroed), trap (H, W, 4) float32."""
     H, W = scene["camera"]["height"], scene["camera"]["width"]
     out = {}
     if rgba8:

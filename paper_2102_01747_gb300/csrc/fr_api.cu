@@ -177,6 +177,20 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
     R.kd = li->k_diffuse;
     R.shadows = li->shadows ? 1 : 0;
     R.bg = make_float4(li->background[0], li->background[1], li->background[2], li->background[3]);
+    if (li->shading != FR_SHADE_LAMBERT && li->shading != FR_SHADE_PHONG)
+        return fail(FR_EINVAL, "shading %d unknown", li->shading);
+    R.shading = li->shading;
+    if (R.shading == FR_SHADE_PHONG) {
+        if (!(li->k_specular >= 0.0f) || !std::isfinite(li->k_specular))
+            return fail(FR_EINVAL, "k_specular must be finite and >= 0");
+        if (!(li->shininess >= 1.0f && li->shininess <= 4096.0f))
+            return fail(FR_EINVAL, "shininess outside 1..4096");
+        if (!(li->reflect_coef >= 0.0f && li->reflect_coef <= 1.0f))
+            return fail(FR_EINVAL, "reflect_coef outside 0..1");
+        R.k_spec = li->k_specular;
+        R.shininess = li->shininess;
+        R.refl_coef = li->reflect_coef;
+    }
 
     R.plane_on = (pl && pl->enabled) ? 1 : 0;
     R.plane = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -256,6 +270,7 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
 {
     const fr_tuning tu = tuning();
     if (tu.single_kernel == 1) {
+        if (R.shading) return fail(FR_ENOTIMPL, "Phong shading runs on the one-ray-per-thread kernel (single_kernel 0)");
         static thread_local fr::BatchArgs A;
         A.reqs[0] = R;
         A.reqs[0].unit_begin = 0;
@@ -331,6 +346,10 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         count = count || q.out.stats != nullptr;
     }
     const fr_tuning tu = tuning();
+    bool any_phong = false;
+    for (const fr::DevReq &R : all) any_phong = any_phong || R.shading != 0;
+    if (any_phong && tu.batch_kernel != 1)
+        return fail(FR_ENOTIMPL, "Phong shading runs on the one-ray-per-thread batch kernel (batch_kernel 1)");
     // largest requests first: the small ones then fill in behind the big ones'
     // slow pixels at the end of the launch (outputs travel with their request)
     std::vector<int> order((size_t)n_reqs);
@@ -362,7 +381,9 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
                 ctas += ctas_of(A.reqs[i]);
             }
             A.total_units = ctas;
-            st = launched(fr::launch_batch_plain(A, ctas, tu.plain_block, tu.plain_unroll, count,
+            bool phong = false;
+            for (int i = 0; i < n; i++) phong = phong || A.reqs[i].shading != 0;
+            st = launched(fr::launch_batch_plain(A, ctas, tu.plain_block, tu.plain_unroll, count, phong,
                                                  (cudaStream_t)stream));
         } else {
             long long units = 0;
@@ -390,6 +411,8 @@ FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plan
     if (st != FR_OK) return st;
     if (params->normal_mode == FR_NORMAL_ANALYTIC)
         return fail(FR_EINVAL, "backward supports the tetrahedral and central normals");
+    if (light && light->shading != FR_SHADE_LAMBERT)
+        return fail(FR_EINVAL, "backward supports Lambert shading");
     if (params->max_iter > fr::kMaxBwdIter)
         return fail(FR_EINVAL, "backward keeps at most %d orbit iterations (max_iter %d)", fr::kMaxBwdIter,
                     params->max_iter);

@@ -29,7 +29,8 @@ constexpr int kTileH = 4;
 
 // statistics slots (same order as FR_STAT_* in include/fr.h)
 constexpr int kStatPrimaryRays = 0, kStatShadowRays = 1, kStatPrimaryDE = 2,
-              kStatNormalDE = 3, kStatShadowDE = 4, kStatOrbit = 5, kNStats = 6;
+              kStatNormalDE = 3, kStatShadowDE = 4, kStatOrbit = 5, kStatReflectRays = 6,
+              kStatReflectDE = 7, kNStats = 8;
 
 constexpr uint32_t kFlagHit = 1u, kFlagFace = 2u, kFlagShadow = 4u;
 
@@ -66,6 +67,9 @@ struct __align__(16) DevReq {
     float4 light;         // normalised direction toward the light
     float4 albedo;
     float ka, kd;
+    float k_spec, shininess;  // Phong highlight weight and exponent
+    float refl_coef;          // weight of the reflected colour
+    int shading;              // 0 Lambert, 1 Phong + reflection bounce
     float pad1, pad2;
     float4 bg;
     uint32_t *rgba8;
@@ -601,6 +605,50 @@ __device__ __forceinline__ float4 shade(const DevReq &R, float3 n, float vis)
     const float diff = ndl > 0.0f ? ndl : 0.0f;
     const float k = fmaf(mul(R.kd, diff), vis, R.ka);
     return make_float4(mul(R.albedo.x, k), mul(R.albedo.y, k), mul(R.albedo.z, k), 1.0f);
+}
+
+// Phong (the closest-hit shader of Sec. 3.1; its helpers are not listed):
+// albedo (ka + kd max(0, n.L) vis) + k_spec vis max(0, r.(-d))^shininess with
+// r = 2 (n.L) n - L the light mirrored about n, no highlight where n.L <= 0.
+__device__ __forceinline__ float3 phong(const DevReq &R, float3 n, float3 d, float vis)
+{
+    const float3 L = v3(R.light);
+    const float ndl = dot3(n, L);
+    const float diff = ndl > 0.0f ? ndl : 0.0f;
+    const float k = fmaf(mul(R.kd, diff), vis, R.ka);
+    float spec = 0.0f;
+    if (ndl > 0.0f) {
+        const float two_ndl = mul(2.0f, ndl);
+        const float3 r = v3(fmaf(n.x, two_ndl, -L.x), fmaf(n.y, two_ndl, -L.y), fmaf(n.z, two_ndl, -L.z));
+        const float rv = -dot3(r, d);
+        spec = powf(rv > 0.0f ? rv : 0.0f, R.shininess);
+    }
+    const float hl = mul(mul(R.k_spec, spec), vis);
+    return v3(fmaf(R.albedo.x, k, hl), fmaf(R.albedo.y, k, hl), fmaf(R.albedo.z, k, hl));
+}
+
+// mirror direction of d about the unit normal n: d - 2 (n.d) n
+__device__ __forceinline__ float3 mirror(float3 d, float3 n)
+{
+    const float m = mul(-2.0f, dot3(n, d));
+    return v3(fmaf(n.x, m, d.x), fmaf(n.y, m, d.y), fmaf(n.z, m, d.z));
+}
+
+// Phong at the hit plus refl_coef * Fresnel-Schlick * (colour along the mirror
+// ray), F = albedo + (1 - albedo) (1 - cos)^5, cos = max(0, -n.rd), per channel.
+__device__ __forceinline__ float4 shade_phong(const DevReq &R, float3 n, float3 rd, float vis, float3 refl)
+{
+    const float3 base = phong(R, n, rd, vis);
+    float c = -dot3(n, rd);
+    c = c > 0.0f ? c : 0.0f;
+    const float u = sub(1.0f, c);
+    const float u2 = mul(u, u);
+    const float w = mul(mul(u2, u2), u);
+    const float fr = fmaf(sub(1.0f, R.albedo.x), w, R.albedo.x);
+    const float fg = fmaf(sub(1.0f, R.albedo.y), w, R.albedo.y);
+    const float fb = fmaf(sub(1.0f, R.albedo.z), w, R.albedo.z);
+    return make_float4(fmaf(mul(R.refl_coef, fr), refl.x, base.x), fmaf(mul(R.refl_coef, fg), refl.y, base.y),
+                       fmaf(mul(R.refl_coef, fb), refl.z, base.z), 1.0f);
 }
 
 // round-half-up of clamp(x, 0, 1) * 255 (NaN -> 0)

@@ -39,9 +39,10 @@ cudaError_t launch_backward(const BwdArgs &A, cudaStream_t s);
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s);
 
 // one-ray-per-thread kernel over A.n_reqs requests in one launch; reqs[r].unit_begin
-// holds request r's first CTA, `ctas` the grid size
+// holds request r's first CTA, `ctas` the grid size; phong: some request uses
+// Phong shading
 cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, int unroll, bool count,
-                               cudaStream_t s);
+                               bool phong, cudaStream_t s);
 
 // lane-state-machine forward kernel without the queue: one pixel per lane, all tiles launched
 cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, cudaStream_t s);

@@ -8,7 +8,7 @@
 
 namespace fr {
 
-template <int KIND, int U, bool COUNT>
+template <int KIND, int U, bool COUNT, bool PHONG>
 __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevReq R)
 {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -19,17 +19,17 @@ __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevR
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
-    if (px < R.width && py < R.height) render_pixel<KIND, U, COUNT>(R, px, py, cnt);
+    if (px < R.width && py < R.height) render_pixel<KIND, U, COUNT, PHONG>(R, px, py, cnt);
     if (COUNT) flush_counters(cnt, R.stats);
 }
 
-template <int KIND, int U, bool COUNT>
+template <int KIND, int U, bool COUNT, bool PHONG = false>
 static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 {
     const long long tiles_y = (R.height + kTileH - 1) / kTileH;
     const long long threads = (long long)R.tiles_x * tiles_y * 32;
     const long long grid = (threads + block - 1) / block;
-    plain_kernel<KIND, U, COUNT><<<(unsigned)grid, block, 0, s>>>(R);
+    plain_kernel<KIND, U, COUNT, PHONG><<<(unsigned)grid, block, 0, s>>>(R);
     return cudaGetLastError();
 }
 
@@ -40,7 +40,7 @@ static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 // CTAs to SMs as they free up, so the requests' slow pixels overlap instead of
 // each launch waiting for its own.  tile_begin of request r (in CTAs) is kept
 // in reqs[r].unit_begin.
-template <int U, bool COUNT>
+template <int U, bool COUNT, bool PHONG>
 __global__ void __launch_bounds__(256) batch_plain_kernel(const __grid_constant__ BatchArgs A)
 {
     const int warps = blockDim.x >> 5;
@@ -63,30 +63,40 @@ __global__ void __launch_bounds__(256) batch_plain_kernel(const __grid_constant_
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
     if (px < R.width && py < R.height) {
         if (R.kind == 0)
-            render_pixel<0, U, COUNT>(R, px, py, cnt);
+            render_pixel<0, U, COUNT, PHONG>(R, px, py, cnt);
         else
-            render_pixel<1, U, COUNT>(R, px, py, cnt);
+            render_pixel<1, U, COUNT, PHONG>(R, px, py, cnt);
     }
     if (COUNT && R.stats) flush_counters(cnt, R.stats);
 }
 
-template <int U, bool COUNT>
+template <int U, bool COUNT, bool PHONG>
 static cudaError_t launch_batch_plain_t(const BatchArgs &A, long long ctas, int block, cudaStream_t s)
 {
-    batch_plain_kernel<U, COUNT><<<(unsigned)ctas, block, 0, s>>>(A);
+    batch_plain_kernel<U, COUNT, PHONG><<<(unsigned)ctas, block, 0, s>>>(A);
     return cudaGetLastError();
 }
 
+// phong: some request of the launch uses Phong shading (the Phong-capable code
+// then serves every request of the launch, at unroll 1)
 cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, int unroll, bool count,
-                               cudaStream_t s)
+                               bool phong, cudaStream_t s)
 {
-    if (count) return launch_batch_plain_t<1, true>(A, ctas, block, s);
-    if (unroll == 2) return launch_batch_plain_t<2, false>(A, ctas, block, s);
-    return launch_batch_plain_t<1, false>(A, ctas, block, s);
+    if (phong) return count ? launch_batch_plain_t<1, true, true>(A, ctas, block, s)
+                            : launch_batch_plain_t<1, false, true>(A, ctas, block, s);
+    if (count) return launch_batch_plain_t<1, true, false>(A, ctas, block, s);
+    if (unroll == 2) return launch_batch_plain_t<2, false, false>(A, ctas, block, s);
+    return launch_batch_plain_t<1, false, false>(A, ctas, block, s);
 }
 
+// Phong requests run the Phong-capable instantiation at unroll 1
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s)
 {
+    if (R.shading) {
+        if (R.kind == 0)
+            return count ? launch_plain_t<0, 1, true, true>(R, block, s) : launch_plain_t<0, 1, false, true>(R, block, s);
+        return count ? launch_plain_t<1, 1, true, true>(R, block, s) : launch_plain_t<1, 1, false, true>(R, block, s);
+    }
     if (count) return R.kind == 0 ? launch_plain_t<0, 1, true>(R, block, s)
                                   : launch_plain_t<1, 1, true>(R, block, s);
     if (R.kind == 0) {

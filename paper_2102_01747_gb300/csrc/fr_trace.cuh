@@ -122,9 +122,85 @@ __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float
     return shade(R, n, vis);
 }
 
-// One pixel: spp samples, mean colour, nearest hit depth, hit point of the
-// nearest hit, OR of the flags; then the stores.
+// The same sample with the closest-hit model of Sec. 3.1 available (requests
+// with R.shading set): after the optional shadow ray a third pass marches the
+// mirror ray from x + 4 eps n; its hit is lit by Phong without a shadow ray or
+// a further bounce (a miss sees the background), and the result is weighted
+// by Fresnel-Schlick in shade_phong.  The two hits' normals share one stencil
+// call, so the DE is still inlined twice.  Kept apart from the Lambert-only
+// loop above, which holds fewer live values.
 template <int KIND, int U, bool COUNT>
+__device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro, float3 rd, float &t_hit,
+                                                     uint32_t &flags, float3 &xhit, Counters &cnt)
+{
+    flags = 0;
+    t_hit = __int_as_float(0x7f800000);
+    float t0, t1, t;
+    bool fp;
+    int steps;
+    if (!bounds(R, ro, rd, t0, t1, fp)) return R.bg;
+    enum { kCamera = 0, kShadow = 1, kReflect = 2 };
+    float3 mro = ro, mrd = rd;  // the ray being marched
+    float3 x = v3(0.0f, 0.0f, 0.0f), n = x;
+    float3 refl = v3(R.bg);     // colour along the mirror ray (Phong shading)
+    uint32_t fl = 0;
+    float vis = 1.0f;
+    int pass = kCamera;
+#pragma unroll 1
+    for (;;) {
+        const bool hit = march<KIND, U, COUNT>(R, mro, mrd, t0, t1, t, steps, cnt,
+                                               pass == kCamera   ? kStatPrimaryDE
+                                               : pass == kShadow ? kStatShadowDE
+                                                                 : kStatReflectDE);
+        if (pass == kShadow) {
+            if (hit) {
+                vis = 0.0f;
+                fl |= kFlagShadow;
+            }
+        } else {
+            if (!hit) {
+                if (pass == kCamera) return R.bg;
+                break;  // the mirror ray sees the background
+            }
+            const float3 xh = along(mro, mrd, t);
+            const bool face = fp && steps == 1;
+            const float3 nh = face ? v3(R.plane_hat) : normal_at<KIND, U, COUNT>(R, xh, mrd, cnt);
+            if (pass == kReflect) {
+                refl = phong(R, nh, mrd, 1.0f);  // no shadow ray, no further bounce
+                break;
+            }
+            x = xh;
+            n = nh;
+            t_hit = t;
+            fl = kFlagHit | (face ? kFlagFace : 0u);
+        }
+        // the next ray from the hit: the shadow ray, then the mirror ray
+        if (pass == kCamera && R.shadows) {
+            if (COUNT) cnt.v[kStatShadowRays] += 1;
+            mro = offset_point(x, n, R.shadow_off);
+            mrd = v3(R.light);
+            if (bounds(R, mro, mrd, t0, t1, fp)) {
+                pass = kShadow;
+                continue;
+            }
+        }
+        if (!R.shading) break;
+        if (COUNT) cnt.v[kStatReflectRays] += 1;
+        mro = offset_point(x, n, R.shadow_off);
+        mrd = mirror(rd, n);
+        if (!bounds(R, mro, mrd, t0, t1, fp)) break;
+        pass = kReflect;
+    }
+    flags = fl;
+    xhit = x;
+    return R.shading ? shade_phong(R, n, rd, vis, refl) : shade(R, n, vis);
+}
+
+// One pixel: spp samples, mean colour, nearest hit depth, hit point of the
+// nearest hit, OR of the flags; then the stores.  PHONG compiles the Phong +
+// mirror-ray path in (requests still choose it with R.shading); without it the
+// Lambert-only code keeps fewer registers.
+template <int KIND, int U, bool COUNT, bool PHONG>
 __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Counters &cnt)
 {
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -137,7 +213,11 @@ __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Co
         uint32_t f;
         camera_ray(R, px, py, s, ro, rd);
         if (COUNT) cnt.v[kStatPrimaryRays] += 1;
-        float4 c = trace_sample<KIND, U, COUNT>(R, ro, rd, t, f, x, cnt);
+        float4 c;
+        if constexpr (PHONG)
+            c = trace_sample_phong<KIND, U, COUNT>(R, ro, rd, t, f, x, cnt);
+        else
+            c = trace_sample<KIND, U, COUNT>(R, ro, rd, t, f, x, cnt);
         acc4(acc, c);
         if ((f & kFlagHit) && t < dmin) {
             dmin = t;

@@ -101,6 +101,10 @@ def _call(F, scene, img=None):
     (lambda s: s["light"].update(dir=(0.0, 0.0, 0.0)), "light direction"),
     (lambda s: s.update(plane={"n": (0.0, 0.0, 0.0), "o": 0.0}), "plane normal"),
     (lambda s: s.update(c=(float("inf"), 0.0, 0.0, 0.0)), "not finite"),
+    (lambda s: s["light"].update(shading="bogus"), None),
+    (lambda s: s["light"].update(shading="phong", shininess=0.5), "shininess"),
+    (lambda s: s["light"].update(shading="phong", reflect_coef=1.5), "reflect_coef"),
+    (lambda s: s["light"].update(shading="phong", k_specular=-1.0), "k_specular"),
     (lambda s: s["camera"].update(width=40000, height=40000, spp=2), "2^31"),
 ])
 def test_bad_julia_arguments_refused(F, mutate, needle):
@@ -111,6 +115,13 @@ def test_bad_julia_arguments_refused(F, mutate, needle):
         p.normal_mode = 7
         st = F.fr_render_julia(p, pl, cam, li, F.fr_image(), None)
         assert st == F.FR_EINVAL and "normal_mode" in F.fr_last_error()
+        return
+    if s["light"].get("shading") == "bogus":
+        s["light"]["shading"] = "lambert"
+        p, pl, cam, li = _structs(s)
+        li.shading = 7
+        st = F.fr_render_julia(p, pl, cam, li, F.fr_image(), None)
+        assert st == F.FR_EINVAL and "shading" in F.fr_last_error()
         return
     st, msg = _call(F, s)
     assert st == F.FR_EINVAL
@@ -199,3 +210,11 @@ def test_autotune_skips_knobs_of_the_other_schedule():
     assert not autotune._in_use("refill_threshold", {"batch_kernel": 1})
     assert autotune._in_use("persist_unroll", {"batch_kernel": 0})
     assert not autotune._in_use("plain_block", {"batch_kernel": 0})
+
+
+def test_backward_refuses_phong(F):
+    """The adjoint covers Lambert shading; every buffer is NULL, so nothing could launch."""
+    s = W.phong(W.julia_256(16, 16))
+    p, pl, cam, li = _structs(s)
+    st = F.fr_render_backward(p, pl, cam, li, None, None, None, None, None)
+    assert st == F.FR_EINVAL and "Lambert" in F.fr_last_error(), F.fr_last_error()

@@ -236,3 +236,51 @@ def test_analytic_normal_render(api, orc, p):
     torch.cuda.synchronize()
     g = gpu(api, s)
     assert np.array_equal(b["rgba8"].cpu().numpy(), g["rgba8"])
+
+
+@pytest.mark.parametrize("case", ["bulb", "julia_cut", "julia_analytic", "bulb_jitter"])
+def test_phong_reflection_render(api, orc, case):
+    """The Phong + Fresnel-weighted mirror-ray model against the oracle's."""
+    if case == "bulb":
+        s = W.phong(W.bulb_1080p(12, 200, 120))
+    elif case == "julia_cut":
+        s = W.phong(dict(W.julia_256(160, 120), plane={"n": (0.2, 0.1, 1.0), "o": 0.1}), reflect_coef=0.6)
+        s["light"]["shadows"] = True
+    elif case == "julia_analytic":
+        s = W.phong(dict(W.julia_256(128, 128), normal_mode="analytic"), k_specular=0.8, shininess=8.0)
+    else:
+        s = W.phong(W.bulb_1080p(3, 96, 64), reflect_coef=1.0)
+        s["camera"]["spp"], s["camera"]["seed"] = 3, 5
+    res, g, o = check(api, orc, s)
+    assert res["hits"] > 1000
+    # the mirror rays do reach the surface somewhere (reflection DE calls and orbit work)
+    assert o["stats"][:, 5].sum() > 1000
+
+
+def test_phong_counters_match_oracle(api, orc):
+    import torch
+
+    s = W.phong(W.bulb_1080p(10, 160, 90))
+    out = api.render(s, rgba8=False, depth=False, stats=True)
+    torch.cuda.synchronize()
+    st = out["stats"].cpu().numpy()
+    os_ = orc.render(s, precision="f32", threads=THREADS)["stats"].sum(0)
+    assert abs(int(st[6]) - int(os_[6])) <= 0.01 * os_[6] + 2  # reflection rays
+    for g_i, o_i in ((2, 0), (3, 1), (4, 2), (5, 3), (7, 5)):
+        assert abs(int(st[g_i]) - int(os_[o_i])) <= 0.02 * os_[o_i] + 10, (g_i, st, os_)
+
+
+def test_phong_refused_by_lane_kernel(api):
+    from paper_2102_01747_gb300 import _ffi as F
+
+    s = W.phong(W.julia_256(32, 32))
+    old = F.fr_get_tuning()
+    t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+    t.single_kernel = 1
+    assert F.fr_set_tuning(t) == F.FR_OK
+    try:
+        with pytest.raises(F.FrError) as e:
+            api.render(s)
+    finally:
+        F.fr_set_tuning(old)
+    assert e.value.status == F.FR_ENOTIMPL
