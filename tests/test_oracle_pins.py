@@ -607,3 +607,34 @@ def test_analytic_normal_matches_fine_central_differences(orc, p):
         cos.append(a @ b)
     cos = np.array(cos)
     assert np.median(cos) > 0.99 and np.mean(cos > 0.99) >= 0.6
+
+
+# ------------------------------------------- c = 0: the Julia set is the unit ball
+@pytest.mark.parametrize("p, mode", [(2, "central"), (3, "tetra"), (2, "analytic")])
+def test_c_zero_julia_set_is_unit_ball(orc, p, mode):
+    """With c = 0 the orbit is z^(p^k), bounded exactly for |z| <= 1: the Julia set
+    is the unit ball and the slice w = 0 the unit sphere.  Its DE near the sphere is
+    (1/2)|z| log|z| (half the distance, Eq. 2 with the listings' 1/2), so the march
+    stops within about 2 eps of the sphere: depth = the ray's entry into the unit
+    sphere, and the normal is radial."""
+    s = W.julia_256(40, 30)
+    s.update(c=(0.0, 0.0, 0.0, 0.0), p=p, normal_mode=mode, max_iter=30,
+             escape_r2=16.0 if p == 2 else 256.0)
+    o = orc.render(s, precision="f64", threads=4)
+    n_hit = 0
+    for idx in range(40 * 30):
+        ro, rd = orc.camera_ray(s, idx % 40, idx // 40)
+        b = ro @ rd
+        disc = b * b - (ro @ ro - 1.0)
+        if disc < 0.02:  # misses, and grazing rays whose entry is ill-conditioned
+            assert disc >= 0.0 or not np.isfinite(o["depth64"][idx])
+            continue
+        t_sphere = -b - math.sqrt(disc)
+        cos_in = math.sqrt(disc)  # |rd . n| at the entry point of a unit sphere
+        assert o["flags"][idx] & 1
+        assert 0.0 <= t_sphere - o["depth64"][idx] <= 2.5 * s["eps"] / cos_in, idx
+        x = ro + o["depth64"][idx] * rd
+        nrm = orc.normal_scene(s, x, rd)
+        assert nrm @ (x / np.linalg.norm(x)) > 0.999, (idx, nrm)
+        n_hit += 1
+    assert n_hit > 300
