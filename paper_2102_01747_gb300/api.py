@@ -171,7 +171,8 @@ def workspace(n_reqs: int, device="cuda") -> torch.Tensor:
 
 
 def render_batch(scenes, outs=None, ws=None, stream=None, **alloc):
-    """Render all scenes in persistent launches over one pixel queue."""
+    """Render all scenes with fr_render_batch (one launch per 64 requests, the
+    schedule set by fr_tuning.batch_kernel)."""
     if outs is None:
         outs = [alloc_image(s, **alloc) for s in scenes]
     if ws is None:
