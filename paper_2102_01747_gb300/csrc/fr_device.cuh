@@ -24,8 +24,10 @@
 
 namespace fr {
 
-constexpr int kTileW = 8;   // a warp covers an 8 x 4 tile of pixels
-constexpr int kTileH = 4;
+// A warp covers a 4 x 8 tile of pixels (4 wide, 8 tall).  Measured against
+// 8 x 4 and 16 x 2 tiles: 4 x 8 is the fastest (1-4 %), 16 x 2 the slowest.
+constexpr int kTileW = 4;
+constexpr int kTileH = 8;
 
 // statistics slots (same order as FR_STAT_* in include/fr.h)
 constexpr int kStatPrimaryRays = 0, kStatShadowRays = 1, kStatPrimaryDE = 2,

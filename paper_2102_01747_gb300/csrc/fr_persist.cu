@@ -273,7 +273,7 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
     begin_de(S, R, S.ro);
 }
 
-// Queue unit u -> (request, pixel).  Units of a request are its 8 x 4 tiles
+// Queue unit u -> (request, pixel).  Units of a request are its 4 x 8 tiles
 // times 32 lanes; slots past the image edge of a ragged tile are empty.
 template <bool COUNT>
 __device__ __forceinline__ void start_pixel(Lane &S, long long u, const DevReq *sreq,
@@ -288,12 +288,14 @@ __device__ __forceinline__ void start_pixel(Lane &S, long long u, const DevReq *
             hi = mid - 1;
     }
     const DevReq &R = sreq[lo];
-    const int local = (int)(u - sbegin[lo]);  // < 2^31: a request has fewer pixels slots
-    const int tile = local >> 5;
-    const int w = local & 31;
-    const int ty = tile / R.tiles_x;
-    const int px = (tile - ty * R.tiles_x) * kTileW + (w & (kTileW - 1));
-    const int py = ty * kTileH + (w / kTileW);
+    // 64-bit: with the ragged tiles' padding a request can hold more than 2^31
+    // slots even though width * height * spp < 2^31
+    const long long local = u - sbegin[lo];
+    const long long tile = local >> 5;
+    const int w = (int)(local & 31);
+    const long long ty = tile / R.tiles_x;
+    const int px = (int)(tile - ty * R.tiles_x) * kTileW + (w & (kTileW - 1));
+    const int py = (int)ty * kTileH + (w / kTileW);
     if (px >= R.width || py >= R.height) return;  // empty slot: the lane stays idle
     S.pix = (uint32_t)px | ((uint32_t)py << 16);
     S.meta = (uint32_t)lo;  // phase idle, sample 0, flags 0

@@ -1,4 +1,4 @@
-// fr_plain.cu -- one ray per thread.  A warp owns an 8 x 4 tile of pixels (so
+// fr_plain.cu -- one ray per thread.  A warp owns a 4 x 8 tile of pixels (so
 // its 32 rays start close together and diverge late); each thread runs its
 // pixel's samples start to finish.  The request rides in the kernel's
 // parameter space (__grid_constant__), read warp-uniformly from the constant

@@ -117,15 +117,32 @@ def test_extreme_shapes(api, orc, w, h):
     assert res["ok"], res
 
 
-def test_largest_image(api, orc):
+@pytest.mark.parametrize("path", ["plain", "lanes", "batch_kernel", "batch_persistent"])
+def test_largest_image(api, orc, path):
     """46340 x 46340 = 2,147,395,600 pixels, just under the 2^31 limit of
-    width*height*spp: 17 GB of outputs; sampled pixels (random, the last row and
-    column, the corners) against the oracle, gathered on the device."""
+    width*height*spp (its padded 4 x 8 tiles hold more than 2^31 pixel slots):
+    17 GB of outputs; sampled pixels (random, the last row and column, the
+    corners) against the oracle, gathered on the device.  Every kernel that
+    renders a single image runs it."""
     import torch
+
+    from paper_2102_01747_gb300 import _ffi as F
 
     w = h = 46340
     s = W.julia_256(w, h)
-    out = api.render(s, rgba8=True, depth=True)
+    old = F.fr_get_tuning()
+    t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+    t.single_kernel = 1 if path == "lanes" else 0
+    t.batch_kernel = 0 if path == "batch_persistent" else 1
+    assert F.fr_set_tuning(t) == F.FR_OK
+    try:
+        if path.startswith("batch"):
+            out = api.render_batch([s], rgba8=True, depth=True)[0]
+        else:
+            out = api.render(s, rgba8=True, depth=True)
+        torch.cuda.synchronize()
+    finally:
+        F.fr_set_tuning(old)
     rng = np.random.default_rng(3)
     px = np.unique(np.r_[rng.integers(0, w * h, 4000), (h - 1) * w + np.arange(0, w, 997),
                          np.arange(0, h, 997) * w + (w - 1), [0, w - 1, (h - 1) * w, w * h - 1]])
