@@ -393,6 +393,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the current launch shape")
+    ap.add_argument("--batch-kernel", type=int, choices=[0, 1], default=None,
+                    help="fix fr_render_batch's schedule (1 one-ray-per-thread kernel over all "
+                         "tiles, 0 persistent kernel); the autotuner then keeps it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -420,6 +423,10 @@ def main():
 
     B.build()
     F.load()
+    if args.batch_kernel is not None:
+        t = F.fr_get_tuning()
+        t.batch_kernel = args.batch_kernel
+        F.check(F.fr_set_tuning(t))
     stream = api.current_stream(dev)
     tstream = torch.cuda.current_stream(dev)
     if args.path == "auto":
@@ -434,7 +441,10 @@ def main():
     if args.path == "batch" and not args.no_autotune:
         from paper_2102_01747_gb300 import autotune
 
-        tuning = autotune.tune(scenes, reps=3)  # untimed search over the launch shape
+        space = dict(autotune.SPACE)
+        if args.batch_kernel is not None:
+            del space["batch_kernel"]
+        tuning = autotune.tune(scenes, reps=3, space=space)  # untimed search over the launch shape
         tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"])}
 
     counts = count_frame(api, torch, scenes)
