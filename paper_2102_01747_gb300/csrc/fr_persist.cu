@@ -3,9 +3,14 @@
 // Why: in the one-ray-per-thread kernel a warp runs until its slowest lane is
 // done, twice over: rays need 1..max_steps march steps, and every DE call
 // needs 1..max_iter orbit steps (Mandelbulb 1080p: 2.7 on average, up to 12).
-// Measured on that kernel at 1080p: 16 of 32 lanes active per issued
+// Measured on that kernel at 1080p: 19 of 32 lanes active per issued
 // instruction; on a batch of small images every launch is as long as its
 // slowest pixel.
+//
+// Outcome, measured on 64 mixed requests: this kernel keeps no more lanes busy
+// (18.5 of 32, like the one-ray-per-thread batch kernel) and its bookkeeping
+// costs 179 thread instructions per orbit iteration against 139, so it is the
+// alternative schedule (fr_tuning.batch_kernel = 0), not the default.
 //
 // How: CTAs stay resident (grid = SMs x resident CTAs).  Each lane holds one
 // pixel's complete state (packed into few registers): its sample, the phase of

@@ -1,8 +1,9 @@
 // fr_static.cu -- fr_render_batch_static: the batched render without a
 // caller-provided workspace, for callers that cannot allocate device memory.
 //
-// The persistent kernel needs one 256-byte queue head per launch of up to 64
-// requests.  fr_render_batch takes that scratch from the caller; this entry
+// The persistent schedule (batch_kernel 0) needs one 256-byte queue head per
+// launch of up to 64 requests.  fr_render_batch takes that scratch from the
+// caller whichever schedule runs; this entry
 // point takes it from a file-scope __device__ array instead, sized for the
 // largest batch fr_render_batch accepts (4096 requests = 64 launches = 16 KB).
 // Every GPU that loads the library holds the array until the process exits.

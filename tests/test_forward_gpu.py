@@ -216,10 +216,20 @@ def test_orbit_trap_output(api, orc, kind):
     got, calib = agree(g, o["trap"]), agree(o["trap"], o64["trap"])
     assert np.all(got >= calib - 0.05), (got, calib)
     assert np.all(np.median(np.abs(g[both] - o["trap"][both]) / (np.abs(o["trap"][both]) + 1e-6), 0) < 1e-3)
-    # the persistent kernel writes the same values
-    b = api.render_batch([s], rgba8=True, depth=True, trap=True)[0]
-    torch.cuda.synchronize()
-    assert np.array_equal(b["trap"].cpu().numpy(), out["trap"].cpu().numpy())
+    # both batch schedules write the same values
+    from paper_2102_01747_gb300 import _ffi as F
+
+    old = F.fr_get_tuning()
+    try:
+        for bk in (1, 0):
+            t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+            t.batch_kernel = bk
+            assert F.fr_set_tuning(t) == F.FR_OK
+            b = api.render_batch([s], rgba8=True, depth=True, trap=True)[0]
+            torch.cuda.synchronize()
+            assert np.array_equal(b["trap"].cpu().numpy(), out["trap"].cpu().numpy()), bk
+    finally:
+        F.fr_set_tuning(old)
 
 
 @pytest.mark.parametrize("p", [2, 3])
