@@ -212,6 +212,8 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
     R.rgba8 = out->rgba8;
     R.rgba = reinterpret_cast<float4 *>(out->rgba);
     R.depth = out->depth;
+    // rows of 4 adjacent pixels start on 16-byte boundaries of both buffers
+    R.quad_store = (cam->width % 4 == 0 && aligned(out->rgba8, 16) && aligned(out->depth, 16)) ? 1 : 0;
     R.saved = reinterpret_cast<float4 *>(out->saved);
     R.stats = out->stats;
     R.trap = reinterpret_cast<float4 *>(out->trap);

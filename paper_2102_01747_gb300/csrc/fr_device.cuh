@@ -72,7 +72,8 @@ struct __align__(16) DevReq {
     float k_spec, shininess;  // Phong highlight weight and exponent
     float refl_coef;          // weight of the reflected colour
     int shading;              // 0 Lambert, 1 Phong + reflection bounce
-    float pad1, pad2;
+    int quad_store;           // rgba8 / depth rows may be written 4 pixels per 16-byte store
+    float pad2;
     float4 bg;
     uint32_t *rgba8;
     float4 *rgba;
@@ -701,16 +702,43 @@ __device__ __forceinline__ void flush_counters(const Counters &c, unsigned long 
     }
 }
 
-// write one finished pixel
-__device__ __forceinline__ void store_pixel(const DevReq &R, int px, int py, float4 acc, float dmin,
-                                            float3 xhit, uint32_t flags)
+// Per-pixel stores of everything but the packed colour and the depth: float
+// RGBA, saved state, orbit trap (16 bytes per pixel each).
+__device__ __forceinline__ void store_pixel_extras(const DevReq &R, long long idx, float4 acc, float3 xhit,
+                                                   uint32_t flags)
 {
-    const long long idx = (long long)py * R.width + px;
-    if (R.rgba8) R.rgba8[idx] = pack_rgba8(acc);
     if (R.rgba) R.rgba[idx] = acc;
-    if (R.depth) R.depth[idx] = dmin;
     if (R.saved) R.saved[idx] = make_float4(xhit.x, xhit.y, xhit.z, __uint_as_float(flags));
     if (R.trap) R.trap[idx] = (flags & kFlagHit) ? orbit_trap(R, xhit) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// Packed colour and depth of a warp's 4 x 8 tile, called by all 32 lanes
+// together (valid: the lane's pixel lies inside the image).  The 4 lanes of a
+// tile row hold 4 adjacent pixels: where the row is complete and the image
+// width and both buffers allow 16-byte alignment (quad_store), the row's
+// first lane gathers them by shuffles and writes one 16-byte store per
+// buffer; otherwise every valid lane writes its own 4 bytes.
+__device__ __forceinline__ void store_rgba8_depth(const DevReq &R, int px, int py, bool valid, uint32_t c8,
+                                                  float d)
+{
+    static_assert(kTileW == 4, "a tile row is one 16-byte quad");
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t c1 = __shfl_down_sync(full, c8, 1), c2 = __shfl_down_sync(full, c8, 2),
+                   c3 = __shfl_down_sync(full, c8, 3);
+    const float d1 = __shfl_down_sync(full, d, 1), d2 = __shfl_down_sync(full, d, 2),
+                d3 = __shfl_down_sync(full, d, 3);
+    const unsigned row = (__ballot_sync(full, valid) >> (lane & ~3)) & 0xfu;
+    const long long idx = (long long)py * R.width + px;
+    if (R.quad_store && row == 0xfu) {
+        if ((lane & 3) == 0) {
+            if (R.rgba8) *reinterpret_cast<uint4 *>(R.rgba8 + idx) = make_uint4(c8, c1, c2, c3);
+            if (R.depth) *reinterpret_cast<float4 *>(R.depth + idx) = make_float4(d, d1, d2, d3);
+        }
+    } else if (valid) {
+        if (R.rgba8) R.rgba8[idx] = c8;
+        if (R.depth) R.depth[idx] = d;
+    }
 }
 
 }  // namespace fr

@@ -19,7 +19,11 @@ __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevR
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
-    if (px < R.width && py < R.height) render_pixel<KIND, U, COUNT, PHONG>(R, px, py, cnt);
+    const bool valid = px < R.width && py < R.height;
+    uint32_t c8 = 0;
+    float depth = 0.0f;
+    if (valid) render_pixel<KIND, U, COUNT, PHONG>(R, px, py, cnt, c8, depth);
+    store_rgba8_depth(R, px, py, valid, c8, depth);
     if (COUNT) flush_counters(cnt, R.stats);
 }
 
@@ -61,12 +65,16 @@ __global__ void __launch_bounds__(256) batch_plain_kernel(const __grid_constant_
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
-    if (px < R.width && py < R.height) {
+    const bool valid = px < R.width && py < R.height;
+    uint32_t c8 = 0;
+    float depth = 0.0f;
+    if (valid) {
         if (R.kind == 0)
-            render_pixel<0, U, COUNT, PHONG>(R, px, py, cnt);
+            render_pixel<0, U, COUNT, PHONG>(R, px, py, cnt, c8, depth);
         else
-            render_pixel<1, U, COUNT, PHONG>(R, px, py, cnt);
+            render_pixel<1, U, COUNT, PHONG>(R, px, py, cnt, c8, depth);
     }
+    store_rgba8_depth(R, px, py, valid, c8, depth);
     if (COUNT && R.stats) flush_counters(cnt, R.stats);
 }
 

@@ -197,11 +197,14 @@ __device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro,
 }
 
 // One pixel: spp samples, mean colour, nearest hit depth, hit point of the
-// nearest hit, OR of the flags; then the stores.  PHONG compiles the Phong +
+// nearest hit, OR of the flags; the per-pixel extras (float RGBA, saved state,
+// trap) are stored here, the packed colour and the depth are returned for the
+// warp's quad store (store_rgba8_depth).  PHONG compiles the Phong +
 // mirror-ray path in (requests still choose it with R.shading); without it the
 // Lambert-only code keeps fewer registers.
 template <int KIND, int U, bool COUNT, bool PHONG>
-__device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Counters &cnt)
+__device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Counters &cnt, uint32_t &c8,
+                                             float &depth)
 {
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float dmin = __int_as_float(0x7f800000);
@@ -225,7 +228,10 @@ __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Co
         }
         fl |= f;
     }
-    store_pixel(R, px, py, mean4(acc, R.spp), dmin, xh, fl);
+    const float4 mean = mean4(acc, R.spp);
+    store_pixel_extras(R, (long long)py * R.width + px, mean, xh, fl);
+    c8 = pack_rgba8(mean);
+    depth = dmin;
 }
 
 }  // namespace fr

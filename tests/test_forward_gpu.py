@@ -294,3 +294,25 @@ def test_phong_refused_by_lane_kernel(api):
     finally:
         F.fr_set_tuning(old)
     assert e.value.status == F.FR_ENOTIMPL
+
+
+@pytest.mark.parametrize("w", [64, 66])
+def test_row_quad_stores_and_unaligned_outputs(api, w):
+    """The one-ray-per-thread kernels write a tile row's 4 packed colours and 4
+    depths with one 16-byte store each when the width is a multiple of 4 and
+    both buffers are 16-byte aligned, else pixel by pixel; output buffers only
+    4-byte aligned (offset by one element) give the same images."""
+    import torch
+
+    s = W.bulb_1080p(10, w, 40)
+    ref = gpu(api, s)
+    n = w * 40
+    big8 = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+    bigd = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+    out = {"rgba8": big8[1:1 + n].view(40, w), "depth": bigd[1:1 + n].view(40, w)}
+    api.render(s, out=out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out["rgba8"].cpu().numpy(), ref["rgba8"])
+    assert np.array_equal(out["depth"].cpu().numpy(), ref["depth"])
+    # nothing written outside the views
+    assert int(big8[0]) == 0 and int(big8[n + 1]) == 0 and float(bigd[0]) == 0.0 and float(bigd[n + 1]) == 0.0
