@@ -218,3 +218,13 @@ def test_backward_refuses_phong(F):
     p, pl, cam, li = _structs(s)
     st = F.fr_render_backward(p, pl, cam, li, None, None, None, None, None)
     assert st == F.FR_EINVAL and "Lambert" in F.fr_last_error(), F.fr_last_error()
+
+
+def test_c_client_compiles_against_the_header():
+    """A plain C99 program (tests/c_client/render_request.c) compiles with
+    -Wall -Wextra -Werror against include/fr.h and links against libfr.so."""
+    import c_client_build
+
+    with tempfile.TemporaryDirectory() as d:
+        exe = c_client_build.build(d)
+        assert os.path.exists(exe)
