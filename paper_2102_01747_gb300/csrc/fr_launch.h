@@ -7,13 +7,13 @@
 
 namespace fr {
 
-// requests per persistent launch: the table rides in the kernel parameters
+// requests per batch launch (either schedule): the table rides in the kernel parameters
 // (64 x sizeof(DevReq) stays well inside the 32 KB parameter limit)
 constexpr int kMaxReqPerLaunch = 64;
 
 struct BatchArgs {
-    unsigned long long *queue;  // queue head (zeroed before the launch)
-    long long total_units;      // pixel slots over all requests
+    unsigned long long *queue;  // queue head of the persistent schedule (zeroed before its launch)
+    long long total_units;      // pixel slots (persistent) or CTAs (batch kernel) over all requests
     int n_reqs;
     int refill_threshold;       // refill a warp once this many lanes are idle
     DevReq reqs[kMaxReqPerLaunch];
