@@ -185,6 +185,37 @@ def test_julia_complex_subspace_bitwise(orc):
             assert (d[j], n[j], tr[j], m2[j]) == want or (math.isnan(d[j]) and math.isnan(want[0]))
 
 
+def _complex_de_cube(z, c, max_iter, esc2):
+    """The listing's degree-3 orbit on C: |f'|^2 picks up 9 |z^2|^2 per step."""
+    dz2, m2, n, trips = 1.0, 0.0, 0, 0
+    for _ in range(max_iter):
+        trips += 1
+        z2 = z * z
+        dz2 *= 9.0 * (z2.real * z2.real + z2.imag * z2.imag)
+        z = z2 * z + c
+        m2 = z.real * z.real + z.imag * z.imag
+        if m2 > esc2:
+            break
+        n += 1
+    return 0.25 * math.log(m2) * math.sqrt(m2 / dz2), n, trips, m2
+
+
+def test_julia_cube_complex_subspace_bitwise(orc):
+    """The listing's own degree (qCube, escape |z|^2 > 256): on span{1, i} the
+    quaternion orbit of z^3 + c is the complex one, bit for bit."""
+    rng = np.random.default_rng(12)
+    s = W.julia_256(8, 8)
+    s.update(p=3, escape_r2=256.0, max_iter=12)
+    for trial in range(4):
+        c = complex(*rng.uniform(-0.7, 0.7, 2))
+        s["c"] = (c.real, c.imag, 0.0, 0.0)
+        pts = np.c_[rng.uniform(-1.4, 1.4, (300, 2)), np.zeros(300)]
+        d, n, tr, m2 = orc.de(s, pts)
+        for j, (x, y, _) in enumerate(pts):
+            want = _complex_de_cube(complex(x, y), c, s["max_iter"], s["escape_r2"])
+            assert (d[j], n[j], tr[j], m2[j]) == want or (math.isnan(d[j]) and math.isnan(want[0]))
+
+
 def test_julia_complex_subspace_float32(orc):
     """Same reduction at float precision, against numpy float32 complex steps."""
     rng = np.random.default_rng(9)
