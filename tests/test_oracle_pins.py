@@ -144,6 +144,25 @@ def test_bulb_power_reduces_to_complex_power(orc):
         assert abs(got[2] - zeta.imag) <= tol
 
 
+def test_bulb_power_composes(orc):
+    """Eq. 1 multiplies both angles by n, so powers compose while no angle wraps:
+    for points near the +y axis with a small azimuth (polar angle b < pi/12,
+    |a| < pi/12), (p^2)^3 = (p^3)^2 = p^6.  Checked in general position, off
+    the half-plane where the complex reduction above applies."""
+    rng = np.random.default_rng(13)
+    for _ in range(2000):
+        b = rng.uniform(1e-3, np.pi / 12)
+        a = rng.uniform(-np.pi / 12, np.pi / 12)
+        r = rng.uniform(0.5, 1.3)
+        # the listing's axes: polar angle from +y, azimuth atan2(x, z)
+        p = r * np.array([np.sin(b) * np.sin(a), np.cos(b), np.sin(b) * np.cos(a)])
+        p6 = orc.bulb_pow(p, 6)
+        p23 = orc.bulb_pow(orc.bulb_pow(p, 2), 3)
+        p32 = orc.bulb_pow(orc.bulb_pow(p, 3), 2)
+        tol = 1e-12 * r**6
+        assert np.allclose(p23, p6, rtol=0, atol=tol) and np.allclose(p32, p6, rtol=0, atol=tol)
+
+
 def test_bulb_power_f32_close_to_f64(orc):
     rng = np.random.default_rng(7)
     for _ in range(500):
