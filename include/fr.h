@@ -277,6 +277,12 @@ FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, 
  *            pixels ignored)
  *   grad     11 floats (device), ADDED to: dc[4], dplane_n[3], dplane_offset,
  *            dlight_dir[3]
+ * The pixels' contributions are summed in double on the device (a per-device
+ * accumulator of the library that every call clears when it ends), so the
+ * result does not depend on the order the GPU runs the pixels in: the same
+ * inputs give the same gradient bits.  Calls that overlap on the GPU (on
+ * different streams, or from different threads) share that accumulator and
+ * race on it; serialise them.
  * Errors: FR_EINVAL (spp != 1, Phong shading, NULL buffers, bad parameters),
  * FR_ECUDA. */
 FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,

@@ -21,8 +21,9 @@
 // Escape counts, hit status and shadow visibility are held fixed.
 //
 // One thread per pixel; the 11 partial sums (dc[4], dn[3], doffset, ddir[3])
-// are reduced per warp with shuffles, per block in shared memory, and added to
-// the caller's gradient with one atomicAdd per block and component.
+// are reduced per warp with shuffles, per block in shared memory, and across
+// blocks in a double accumulator that the last block adds to the caller's
+// gradient (reproducible bits; see backward_kernel).
 #include "fr_launch.h"
 #include "fr_trace.cuh"
 
@@ -186,6 +187,11 @@ __device__ void pixel_grad(const BwdArgs &A, int px, int py, float gsum[11])
     gsum[10] += act * (n.z - L.z * ndl) / A.light_norm;
 }
 
+// The per-call gradient accumulator of the device (11 doubles) and the count
+// of finished blocks; both return to zero at the end of every call.
+__device__ double g_bwd_acc[11];
+__device__ unsigned int g_bwd_done;
+
 template <int P>
 __global__ void __launch_bounds__(256) backward_kernel(const __grid_constant__ BwdArgs A)
 {
@@ -209,10 +215,33 @@ __global__ void __launch_bounds__(256) backward_kernel(const __grid_constant__ B
         if (lane == 0) part[warp][k] = v;
     }
     __syncthreads();
+    // Block sums go into a double accumulator, so their order (which block
+    // finishes first) moves the total by about 1e-16 relative, far below the
+    // float rounding it gets at the end: the same inputs give the same
+    // gradient bits (unless a total falls that close to a float rounding
+    // boundary).  The last block to finish converts the totals to float once,
+    // adds them to the caller's gradient and clears the accumulator for the
+    // next call.  No block waits for another: the last one is the one whose
+    // ticket completes the count (fence, then count).
     if (threadIdx.x < 11) {
         float v = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += part[w][threadIdx.x];
-        if (v != 0.0f) atomicAdd(A.grad + threadIdx.x, v);
+        if (v != 0.0f) atomicAdd(g_bwd_acc + threadIdx.x, (double)v);
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(&g_bwd_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x < 11) {
+            // read and clear in one step
+            const unsigned long long bits =
+                atomicExch(reinterpret_cast<unsigned long long *>(g_bwd_acc + threadIdx.x), 0ull);
+            A.grad[threadIdx.x] += (float)__longlong_as_double((long long)bits);
+        }
+        if (threadIdx.x == 0) g_bwd_done = 0u;
     }
 }
 

@@ -30,6 +30,20 @@ def stable_mask(orc, scene):
                                          10 * scene["eps"])
 
 
+def well_conditioned(orc, scene, min_cos=0.1):
+    """Pixels whose implicit derivative is well conditioned: the depth moves as
+    1 / (grad d . rd), so grazing hits (|n . rd| < min_cos, silhouettes) amplify
+    any float error in the gradient of the DE; cut faces and misses are kept."""
+    r = orc.render(scene, precision="f64", threads=8)
+    keep = np.ones(len(r["flags"]), bool)
+    w = scene["camera"]["width"]
+    for i in np.flatnonzero((r["flags"] & 1) & ~(r["flags"] & 2)):
+        ro, rd = orc.camera_ray(scene, i % w, i // w)
+        nrm = orc.normal_scene(scene, ro + r["depth64"][i] * rd, rd)
+        keep[i] = abs(nrm @ rd) >= min_cos
+    return keep
+
+
 def gpu_grad(mods, scene, d_rgba, d_depth):
     torch, api, autograd = mods
     out = api.render(scene, rgba8=False, rgba=True, depth=True, saved=True)
@@ -62,6 +76,52 @@ def test_gpu_adjoint_matches_fp64_reference(mods, orc, eps, normal):
     assert cos >= 1 - tol**2 and rel <= tol, (g, ref, cos, rel)
     # the light gradient does not depend on the hit depth: tighter
     assert np.linalg.norm(g[8:] - ref[8:]) <= tol * np.linalg.norm(ref[8:]) + 1e-6
+
+
+@pytest.mark.parametrize("variant", ["cube", "shadowed", "no_cut", "jittered_camera"])
+def test_gpu_adjoint_variants(mods, orc, variant):
+    """The adjoint beyond the workload's setting: the listing's degree 3, shadow
+    rays (visibility held fixed), no cut plane, another camera.  The degree-3
+    orbit (escape |z|^2 > 256) is compared at eps = 1e-3: at 1e-5 the float
+    gradient of its DE near the surface drifts from the double one (19 % over
+    all pixels), while at 1e-3 they agree to 0.1 %.  Grazing hits
+    (silhouettes, where the implicit derivative divides by a vanishing
+    grad d . rd) are left out of the cotangents."""
+    s, _ = W.diff_julia(W.BASE_SEED, 112, 96)
+    s["eps"], s["max_steps"] = (1e-3 if variant == "cube" else 1e-5), 2000
+    if variant == "cube":
+        s.update(p=3, escape_r2=256.0, max_iter=12, c=(-0.1, 0.55, 0.3, 0.1))
+    elif variant == "shadowed":
+        s["light"]["shadows"] = True
+    elif variant == "no_cut":
+        s["plane"] = None
+    else:
+        s["camera"]["eye"] = (-1.1, 0.4, 2.6)
+    n = 112 * 96
+    torch, api, _ = mods
+    fwd = api.render(s, rgba8=False, rgba=True, depth=True, saved=True)
+    torch.cuda.synchronize()
+    gpu_flags = fwd["saved"].cpu().numpy().reshape(-1, 4)[:, 3].view(np.uint32)
+    o64 = orc.render(s, precision="f64", threads=8)
+    # pixels in the same state on the GPU and in both oracle precisions, away
+    # from grazing hits
+    mask = stable_mask(orc, s) & well_conditioned(orc, s) & (gpu_flags == o64["flags"].astype(np.uint32))
+    rng = np.random.default_rng(17)
+    d_rgba = rng.standard_normal((n, 4)) * mask[:, None]
+    d_rgba[:, 3] = 0.0
+    d_depth = 0.3 * rng.standard_normal(n) * mask
+    g, _ = gpu_grad(mods, s, d_rgba.astype(np.float32), d_depth.astype(np.float32))
+    ref = orc.julia_grad(s, d_rgba.astype(np.float32).astype(np.float64),
+                         d_depth.astype(np.float32).astype(np.float64), threads=8)
+    cos = g @ ref / np.linalg.norm(g) / np.linalg.norm(ref)
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    # without the cut every hit lies on the fractal surface, where the float
+    # reverse sweep through the orbit loses more digits than on the workload's
+    # cut face (measured: 4 % apart, cosine 0.9993)
+    tol = 5e-2 if variant == "no_cut" else 2e-2
+    assert cos >= 1 - tol**2 and rel <= tol, (variant, g, ref, cos, rel)
+    if variant == "no_cut":
+        assert np.all(g[4:8] == 0.0) and np.all(ref[4:8] == 0.0)
 
 
 def test_cut_face_offset_gradient(mods, orc):
@@ -127,3 +187,26 @@ def test_adam_recovers_hidden_c(mods):
             first = float(loss.detach())
     err = np.linalg.norm(c.detach().numpy() - c_star)
     assert err < 2e-2, (err, first, float(loss.detach()))
+
+
+def test_gradient_bits_are_reproducible(mods):
+    """The adjoint's cross-block sum is done in double and rounded once, so
+    repeated calls on the same inputs give the same float bits."""
+    torch, api, autograd = mods
+    s, _ = W.diff_julia(W.BASE_SEED, 256, 256)
+    out = api.render(s, rgba8=False, rgba=True, depth=True, saved=True)
+    rng = np.random.default_rng(3)
+    d_rgba = torch.tensor(rng.standard_normal((256 * 256, 4)).astype(np.float32), device="cuda")
+    d_depth = torch.tensor(rng.standard_normal(256 * 256).astype(np.float32), device="cuda")
+    grads = []
+    for _ in range(6):
+        g = autograd.backward_raw(s, out["saved"], d_rgba, d_depth)
+        torch.cuda.synchronize()
+        grads.append(g.cpu().numpy())
+    assert all(np.array_equal(grads[0], g) for g in grads[1:])
+    # accumulation: a second call into the same buffer adds the same vector
+    acc = torch.zeros(11, dtype=torch.float32, device="cuda")
+    autograd.backward_raw(s, out["saved"], d_rgba, d_depth, grad=acc)
+    autograd.backward_raw(s, out["saved"], d_rgba, d_depth, grad=acc)
+    torch.cuda.synchronize()
+    assert np.array_equal(acc.cpu().numpy(), (grads[0] + grads[0]).astype(np.float32))
