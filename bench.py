@@ -160,7 +160,8 @@ def run_reference(args, scenes, desc, rank, world):
     n = sum(s["camera"]["width"] * s["camera"]["height"] for s in scenes)
     stride = max(1, n // 2_000_000)
     samples = _oracle_sample(scenes, stride)
-    _oracle_rays(oracle, scenes, _oracle_sample(scenes, stride * 16), threads)  # warm-up
+    for _ in range(args.warmup):  # untimed warm-up steps on the same sample
+        _oracle_rays(oracle, scenes, samples, threads)
     t0 = time.perf_counter()
     rays = 0
     for _ in range(args.steps):
