@@ -102,3 +102,41 @@ def test_static_batch_graph(env):
         ref = api.render(sc, rgba8=True, depth=True)
         torch.cuda.synchronize()
         assert torch.equal(ref["rgba8"], o["rgba8"]) and torch.equal(ref["depth"], o["depth"])
+
+
+def test_backward_graph(env):
+    """Forward (with saved state) and adjoint captured together: every replay
+    adds the same gradient bits to the accumulator (the adjoint's device-side
+    double accumulator is cleared by each launch)."""
+    torch, F, api = env
+    s, _ = W.diff_julia(W.BASE_SEED, 128, 96)
+    out = api.alloc_image(s, rgba8=False, rgba=True, depth=True, saved=True)
+    n = 128 * 96
+    rng = np.random.default_rng(2)
+    d_rgba = torch.tensor(rng.standard_normal((n, 4)).astype(np.float32), device="cuda")
+    d_depth = torch.tensor(rng.standard_normal(n).astype(np.float32), device="cuda")
+    grad = torch.zeros(11, dtype=torch.float32, device="cuda")
+    img = api.image_struct(out)
+    args = (api.julia_params(s), api.plane_struct(s), api.camera_struct(s), api.light_struct(s), img)
+
+    def call(st):
+        F.check(F.fr_render_julia(*args, st.cuda_stream))
+        F.check(F.fr_render_backward(args[0], args[1], args[2], args[3], out["saved"].data_ptr(),
+                                     d_rgba.data_ptr(), d_depth.data_ptr(), grad.data_ptr(), st.cuda_stream))
+
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        call(st)
+    st.synchronize()
+    once = grad.clone()
+    grad.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        call(st)
+    grad.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(grad, once)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(grad, once + once)
