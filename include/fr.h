@@ -104,10 +104,8 @@ typedef struct {
  *         normal scheme, no shadow ray, no further bounce), background rgb on
  *         a miss
  *   miss: rgba = background
- * The Phong model runs on the one-ray-per-thread kernels (fr_render_julia,
- * fr_render_mandelbulb with single_kernel 0, fr_render_batch with
- * batch_kernel 1); the lane kernels refuse it with FR_ENOTIMPL and the adjoint
- * with FR_EINVAL. */
+ * Every forward kernel runs both models; the adjoint (fr_render_backward)
+ * refuses the Phong model with FR_EINVAL. */
 typedef struct {
     float dir[3];            /* toward the light; normalised here, must be non-zero */
     float albedo[3];

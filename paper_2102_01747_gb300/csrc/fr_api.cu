@@ -272,7 +272,6 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
 {
     const fr_tuning tu = tuning();
     if (tu.single_kernel == 1) {
-        if (R.shading) return fail(FR_ENOTIMPL, "Phong shading runs on the one-ray-per-thread kernel (single_kernel 0)");
         static thread_local fr::BatchArgs A;
         A.reqs[0] = R;
         A.reqs[0].unit_begin = 0;
@@ -280,7 +279,8 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
         A.total_units = R.n_units;
         A.refill_threshold = 1;
         A.queue = nullptr;
-        return launched(fr::launch_lanes(A, tu.plain_block, tu.persist_unroll, count, (cudaStream_t)stream));
+        return launched(fr::launch_lanes(A, tu.plain_block, tu.persist_unroll, count, R.shading != 0,
+                                         (cudaStream_t)stream));
     }
     return launched(fr::launch_plain(R, tu.plain_block, tu.plain_unroll, count, (cudaStream_t)stream));
 }
@@ -348,10 +348,7 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         count = count || q.out.stats != nullptr;
     }
     const fr_tuning tu = tuning();
-    bool any_phong = false;
-    for (const fr::DevReq &R : all) any_phong = any_phong || R.shading != 0;
-    if (any_phong && tu.batch_kernel != 1)
-        return fail(FR_ENOTIMPL, "Phong shading runs on the one-ray-per-thread batch kernel (batch_kernel 1)");
+
     // largest requests first: the small ones then fill in behind the big ones'
     // slow pixels at the end of the launch (outputs travel with their request)
     std::vector<int> order((size_t)n_reqs);
@@ -395,8 +392,10 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
                 units += A.reqs[i].n_units;
             }
             A.total_units = units;
+            bool phong = false;
+            for (int i = 0; i < n; i++) phong = phong || A.reqs[i].shading != 0;
             st = launched(fr::launch_persist(A, tu.persist_block, tu.persist_ctas_per_sm, tu.persist_unroll,
-                                             count, (cudaStream_t)stream));
+                                             count, phong, (cudaStream_t)stream));
         }
         if (st != FR_OK) return st;
     }

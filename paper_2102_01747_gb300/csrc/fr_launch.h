@@ -45,10 +45,10 @@ cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, in
                                bool phong, cudaStream_t s);
 
 // lane-state-machine forward kernel without the queue: one pixel per lane, all tiles launched
-cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, cudaStream_t s);
+cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, bool phong, cudaStream_t s);
 
 // persistent forward kernel over A.n_reqs requests (memset of the queue head + launch)
-cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int unroll, bool count,
+cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int unroll, bool count, bool phong,
                            cudaStream_t s);
 
 }  // namespace fr

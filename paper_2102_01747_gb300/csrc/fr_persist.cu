@@ -47,7 +47,7 @@ enum : uint32_t { PH_IDLE = 0, PH_PRIMARY = 1, PH_NORMAL = 2, PH_SHADOW = 3 };
 // Lane state.  Small integers are packed:
 //   pix  = px | py << 16
 //   meta = req (bits 0-7) | phase (8-9) | tap (10-12) | fp (13) | sample (14-20)
-//          | sample flags (21-23) | pixel flags (24-26)
+//          | sample flags (21-23) | pixel flags (24-26) | mirror stage (27)
 //   cnt  = orbit steps of the current DE (bits 0-10) | march steps (11-30)
 // During the normal phase `ro` holds the current stencil tap point (the camera
 // ray's origin is no longer needed there).
@@ -55,8 +55,9 @@ struct Lane {
     uint32_t pix, meta, cnt;
     float3 ro, rd;
     float t, t1, thit;
-    float3 x;         // hit point of the current sample
+    float3 x;         // hit point of the current sample (of the mirror ray in the mirror stage)
     float3 g;         // stencil sum, then the unit normal
+    float3 n0;        // Phong shading: the camera hit's normal while the mirror ray runs
     Orbit o;
     float4 acc;       // colour summed over samples
     float dmin;       // nearest hit over samples
@@ -74,6 +75,9 @@ __device__ __forceinline__ void L_set_sample(Lane &S, int k) { S.meta = (S.meta 
 __device__ __forceinline__ uint32_t L_sflags(const Lane &S) { return (S.meta >> 21) & 7u; }
 __device__ __forceinline__ void L_set_sflags(Lane &S, uint32_t f) { S.meta = (S.meta & ~(7u << 21)) | (f << 21); }
 __device__ __forceinline__ uint32_t L_pflags(const Lane &S) { return (S.meta >> 24) & 7u; }
+// mirror stage: the march / stencil in progress belongs to the Phong model's mirror ray
+__device__ __forceinline__ bool L_rf(const Lane &S) { return (S.meta >> 27) & 1u; }
+__device__ __forceinline__ void L_set_rf(Lane &S, bool f) { S.meta = (S.meta & ~(1u << 27)) | ((uint32_t)f << 27); }
 __device__ __forceinline__ int L_px(const Lane &S) { return (int)(S.pix & 0xffffu); }
 __device__ __forceinline__ int L_py(const Lane &S) { return (int)(S.pix >> 16); }
 __device__ __forceinline__ int L_it(const Lane &S) { return (int)(S.cnt & 0x7ffu); }
@@ -160,31 +164,81 @@ __device__ void begin_samples(Lane &S, const DevReq &R, PixCount &pc)
     store_and_idle<COUNT>(S, R, pc);
 }
 
+// the camera ray of the current sample hit at S.thit, S.x: keep the nearest
+// hit over the samples (depth, saved hit point, orbit trap)
+__device__ __forceinline__ void record_hit(Lane &S, const DevReq &R)
+{
+    if (S.thit < S.dmin) {
+        S.dmin = S.thit;
+        if (R.saved) {
+            float *sv = reinterpret_cast<float *>(R.saved + pixel_index(R, S));
+            sv[0] = S.x.x;
+            sv[1] = S.x.y;
+            sv[2] = S.x.z;
+        }
+        if (R.trap) R.trap[pixel_index(R, S)] = orbit_trap(R, S.x);
+    }
+}
+
 template <bool COUNT>
 __device__ __forceinline__ void finish_sample(Lane &S, const DevReq &R, float4 c, bool hit, PixCount &pc)
 {
     acc4(S.acc, c);
-    if (hit) {
-        if (S.thit < S.dmin) {
-            S.dmin = S.thit;
-            if (R.saved) {
-                float *sv = reinterpret_cast<float *>(R.saved + pixel_index(R, S));
-                sv[0] = S.x.x;
-                sv[1] = S.x.y;
-                sv[2] = S.x.z;
-            }
-            if (R.trap) R.trap[pixel_index(R, S)] = orbit_trap(R, S.x);
-        }
-        S.meta |= L_sflags(S) << 24;
-    }
+    if (hit) S.meta |= L_sflags(S) << 24;
     L_set_sample(S, L_sample(S) + 1);
     begin_samples<COUNT>(S, R, pc);
 }
 
-// the unit normal is in S.g: cast the shadow ray, or shade the sample
+// Phong shading of the sample once the colour along its mirror ray is known
 template <bool COUNT>
+__device__ __forceinline__ void finish_phong(Lane &S, const DevReq &R, float3 refl, PixCount &pc)
+{
+    float3 ro, rd;
+    camera_ray(R, L_px(S), L_py(S), L_sample(S), ro, rd);
+    const float vis = (L_sflags(S) & kFlagShadow) ? 0.0f : 1.0f;
+    L_set_rf(S, false);
+    finish_sample<COUNT>(S, R, shade_phong(R, S.n0, rd, vis, refl), true, pc);
+}
+
+// Phong shading: cast the mirror ray of the camera ray about the hit's normal
+// S.g from x + 4 eps n (a miss, or an empty interval, sees the background)
+template <bool COUNT>
+__device__ __forceinline__ void start_mirror(Lane &S, const DevReq &R, PixCount &pc)
+{
+    float3 ro, rd;
+    camera_ray(R, L_px(S), L_py(S), L_sample(S), ro, rd);
+    S.n0 = S.g;
+    if (COUNT) pc.v[kStatReflectRays] += 1;
+    const float3 mo = offset_point(S.x, S.n0, R.shadow_off);
+    const float3 md = mirror(rd, S.n0);
+    float t0, t1;
+    bool fp;
+    if (!bounds(R, mo, md, t0, t1, fp)) {
+        finish_phong<COUNT>(S, R, v3(R.bg), pc);
+        return;
+    }
+    L_set_rf(S, true);
+    L_set_phase(S, PH_PRIMARY);
+    L_set_fp(S, fp);
+    S.cnt = 0;
+    S.ro = mo;
+    S.rd = md;
+    S.t = t0;
+    S.t1 = t1;
+    begin_de(S, R, along(mo, md, t0));
+}
+
+// the unit normal is in S.g: cast the shadow ray, then (Phong) the mirror ray,
+// or shade the sample; in the mirror stage it is the mirror hit's normal
+template <bool COUNT, bool PHONG>
 __device__ __forceinline__ void after_normal(Lane &S, const DevReq &R, PixCount &pc)
 {
+    if constexpr (PHONG) {
+        if (L_rf(S)) {  // the mirror ray's hit, lit by Phong without a shadow ray
+            finish_phong<COUNT>(S, R, phong(R, S.g, S.rd, 1.0f), pc);
+            return;
+        }
+    }
     if (R.shadows) {
         const float3 L = v3(R.light);
         const float3 so = offset_point(S.x, S.g, R.shadow_off);
@@ -202,11 +256,18 @@ __device__ __forceinline__ void after_normal(Lane &S, const DevReq &R, PixCount 
             return;
         }
     }
+    if constexpr (PHONG) {
+        if (R.shading) {
+            start_mirror<COUNT>(S, R, pc);
+            return;
+        }
+    }
     finish_sample<COUNT>(S, R, shade(R, S.g, 1.0f), true, pc);
 }
 
 // A DE call of the lane has finished with distance d: advance its ray.
-template <bool COUNT>
+// PHONG compiles the mirror stage in (requests still choose it with R.shading).
+template <bool COUNT, bool PHONG>
 __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
 {
     const uint32_t phase = L_phase(S);
@@ -223,13 +284,14 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
             return;
         }
         S.g = finish_normal(S.g, S.rd);
-        after_normal<COUNT>(S, R, pc);
+        after_normal<COUNT, PHONG>(S, R, pc);
         return;
     }
     // one step of a camera or shadow march
     const int steps = L_steps(S) + 1;
     S.cnt = (uint32_t)steps << 11;
-    if (COUNT) pc.v[phase == PH_PRIMARY ? kStatPrimaryDE : kStatShadowDE] += 1;
+    const bool rf = PHONG && L_rf(S);
+    if (COUNT) pc.v[phase == PH_SHADOW ? kStatShadowDE : (rf ? kStatReflectDE : kStatPrimaryDE)] += 1;
     bool hit = d < R.eps;
     bool miss = false;
     if (!hit) {
@@ -245,20 +307,35 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
     }
     if (phase == PH_SHADOW) {
         if (hit) L_set_sflags(S, L_sflags(S) | kFlagShadow);
+        if constexpr (PHONG) {
+            if (R.shading) {
+                start_mirror<COUNT>(S, R, pc);
+                return;
+            }
+        }
         finish_sample<COUNT>(S, R, shade(R, S.g, hit ? 0.0f : 1.0f), true, pc);
         return;
     }
     if (miss) {
+        if constexpr (PHONG) {
+            if (rf) {
+                finish_phong<COUNT>(S, R, v3(R.bg), pc);  // the mirror ray sees the background
+                return;
+            }
+        }
         finish_sample<COUNT>(S, R, R.bg, false, pc);
         return;
     }
-    S.thit = S.t;
     S.x = along(S.ro, S.rd, S.t);
-    L_set_sflags(S, kFlagHit);
+    if (!rf) {
+        S.thit = S.t;
+        L_set_sflags(S, kFlagHit);
+        record_hit(S, R);
+    }
     if (L_fp(S) && steps == 1) {  // first sample on the cut plane is inside: the cut face
         S.g = v3(R.plane_hat);
-        L_set_sflags(S, kFlagHit | kFlagFace);
-        after_normal<COUNT>(S, R, pc);
+        if (!rf) L_set_sflags(S, kFlagHit | kFlagFace);
+        after_normal<COUNT, PHONG>(S, R, pc);
         return;
     }
     if (R.kind == 0 && R.normal_mode == 2) {  // analytic normal: one orbit with tangents, no stencil
@@ -268,7 +345,7 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
             pc.v[kStatNormalDE] += 1;
             pc.v[kStatOrbit] += trips;
         }
-        after_normal<COUNT>(S, R, pc);
+        after_normal<COUNT, PHONG>(S, R, pc);
         return;
     }
     L_set_phase(S, PH_NORMAL);
@@ -321,7 +398,7 @@ __device__ __forceinline__ void start_pixel(Lane &S, long long u, const DevReq *
 // takes the 32 pixel slots of one tile at launch (grid = all tiles) and ends
 // when its lanes are done.  Lanes of different phases still share one DE code
 // path and never wait for each other's orbits, but nothing is refilled.
-template <int KJ, bool COUNT, bool REFILL>
+template <int KJ, bool COUNT, bool REFILL, bool PHONG>
 __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(const __grid_constant__ BatchArgs A)
 {
     extern __shared__ float4 smem[];
@@ -395,7 +472,7 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
                 }
                 if (done) {
                     if (COUNT) pc.v[kStatOrbit] += L_it(S);
-                    advance<COUNT>(S, R, julia_dist(S.o), pc);
+                    advance<COUNT, PHONG>(S, R, julia_dist(S.o), pc);
                 }
             } else {
                 const float3 cpt = (L_phase(S) == PH_NORMAL) ? S.ro : along(S.ro, S.rd, S.t);
@@ -406,41 +483,46 @@ __global__ void __launch_bounds__(256, FR_PERSIST_MIN_BLOCKS) persist_kernel(con
                 S.cnt++;
                 if ((S.o.m > R.esc2) || (L_it(S) >= R.max_iter)) {
                     if (COUNT) pc.v[kStatOrbit] += L_it(S);
-                    advance<COUNT>(S, R, bulb_dist(S.o), pc);
+                    advance<COUNT, PHONG>(S, R, bulb_dist(S.o), pc);
                 }
             }
         }
     }
 }
 
-template <int KJ, bool COUNT, bool REFILL>
+template <int KJ, bool COUNT, bool REFILL, bool PHONG = false>
 static cudaError_t launch_persist_t(const BatchArgs &A, int block, int ctas_per_sm, cudaStream_t s)
 {
     const size_t smem = (size_t)A.n_reqs * sizeof(DevReq);
     if (!REFILL) {
         const long long grid = (A.total_units + block - 1) / block;
-        persist_kernel<KJ, COUNT, false><<<(unsigned)grid, block, smem, s>>>(A);
+        persist_kernel<KJ, COUNT, false, PHONG><<<(unsigned)grid, block, smem, s>>>(A);
         return cudaGetLastError();
     }
     int dev = 0, sms = 0, fit = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, persist_kernel<KJ, COUNT, true>, block, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, persist_kernel<KJ, COUNT, true, PHONG>, block,
+                                                           smem)) !=
         cudaSuccess)
         return e;
     if (fit < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < fit) ? ctas_per_sm : fit;
     if ((e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    persist_kernel<KJ, COUNT, true><<<sms * per_sm, block, smem, s>>>(A);
+    persist_kernel<KJ, COUNT, true, PHONG><<<sms * per_sm, block, smem, s>>>(A);
     return cudaGetLastError();
 }
 
 static_assert(sizeof(BatchArgs) <= 32764, "the request table must fit the kernel parameter space");
 
-cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int unroll, bool count,
+// phong: some request of the launch uses Phong shading (the Phong-capable
+// instantiation then serves every request of the launch, at unroll 4)
+cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int unroll, bool count, bool phong,
                            cudaStream_t s)
 {
+    if (phong) return count ? launch_persist_t<4, true, true, true>(A, block, ctas_per_sm, s)
+                            : launch_persist_t<4, false, true, true>(A, block, ctas_per_sm, s);
     if (count) return launch_persist_t<4, true, true>(A, block, ctas_per_sm, s);
     if (unroll == 8) return launch_persist_t<8, false, true>(A, block, ctas_per_sm, s);
     if (unroll == 4) return launch_persist_t<4, false, true>(A, block, ctas_per_sm, s);
@@ -448,8 +530,10 @@ cudaError_t launch_persist(const BatchArgs &A, int block, int ctas_per_sm, int u
     return launch_persist_t<1, false, true>(A, block, ctas_per_sm, s);
 }
 
-cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, cudaStream_t s)
+cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, bool phong, cudaStream_t s)
 {
+    if (phong) return count ? launch_persist_t<4, true, false, true>(A, block, 0, s)
+                            : launch_persist_t<4, false, false, true>(A, block, 0, s);
     if (count) return launch_persist_t<4, true, false>(A, block, 0, s);
     if (unroll == 8) return launch_persist_t<8, false, false>(A, block, 0, s);
     if (unroll == 2) return launch_persist_t<2, false, false>(A, block, 0, s);

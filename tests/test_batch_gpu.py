@@ -212,29 +212,22 @@ def test_autotune_keeps_images_and_applies_its_choice(api):
         same_or_close(_np([api.render(s, rgba8=True, depth=True)])[0], b)
 
 
-def test_phong_requests_in_a_batch(api, orc):
-    """Phong requests mixed with Lambert ones: the batch kernel's images equal the
-    single-request kernel's and the oracle's; the persistent schedule refuses
-    the Phong model."""
-    from paper_2102_01747_gb300 import _ffi as F
+def test_phong_requests_in_a_batch(api, orc, schedule):
+    """Phong requests mixed with Lambert ones, under both schedules: the images
+    equal the single-request kernel's and the oracle's, and the counters too."""
+    import torch
 
     scenes = small_mixed(6, seed=13)
     scenes = [W.phong(s) if i % 3 == 0 else s for i, s in enumerate(scenes)]
-    old = tuned(F, batch_kernel=1)
-    try:
-        batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
-    finally:
-        F.fr_set_tuning(old)
+    batch = _np(api.render_batch(scenes, rgba8=True, depth=True))
     for s, b in zip(scenes, batch):
         same_or_close(_np([api.render(s, rgba8=True, depth=True)])[0], b)
         if s["light"].get("shading") == "phong":
             o = orc.render(s, precision="f32", threads=THREADS)
             res = compare(b["rgba8"].reshape(-1), b["depth"].reshape(-1), o["rgba8"], o["depth"])
             assert res["ok"], res
-    old = tuned(F, batch_kernel=0)
-    try:
-        with pytest.raises(F.FrError) as e:
-            api.render_batch(scenes, rgba8=True, depth=True)
-    finally:
-        F.fr_set_tuning(old)
-    assert e.value.status == F.FR_ENOTIMPL
+    s = scenes[0]
+    p = api.render(s, rgba8=False, depth=False, stats=True)
+    b = api.render_batch([s], rgba8=False, depth=False, stats=True)[0]
+    torch.cuda.synchronize()
+    assert np.array_equal(p["stats"].cpu().numpy(), b["stats"].cpu().numpy())

@@ -280,39 +280,22 @@ def test_phong_counters_match_oracle(api, orc):
         assert abs(int(st[g_i]) - int(os_[o_i])) <= 0.02 * os_[o_i] + 10, (g_i, st, os_)
 
 
-def test_phong_refused_by_lane_kernel(api):
+def test_phong_on_the_lane_kernel(api):
+    """The lane state machine (single_kernel 1) runs the mirror stage too and
+    gives the one-ray-per-thread kernel's images bit for bit."""
     from paper_2102_01747_gb300 import _ffi as F
 
-    s = W.phong(W.julia_256(32, 32))
+    scenes = [W.phong(W.bulb_1080p(12, 120, 72)),
+              W.phong(dict(W.julia_256(96, 64), plane={"n": (0.2, 0.1, 1.0), "o": 0.1}), reflect_coef=0.6)]
+    scenes[1]["light"]["shadows"] = True
+    refs = [gpu(api, s) for s in scenes]
     old = F.fr_get_tuning()
     t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
     t.single_kernel = 1
     assert F.fr_set_tuning(t) == F.FR_OK
     try:
-        with pytest.raises(F.FrError) as e:
-            api.render(s)
+        got = [gpu(api, s) for s in scenes]
     finally:
         F.fr_set_tuning(old)
-    assert e.value.status == F.FR_ENOTIMPL
-
-
-@pytest.mark.parametrize("w", [64, 66])
-def test_row_quad_stores_and_unaligned_outputs(api, w):
-    """The one-ray-per-thread kernels write a tile row's 4 packed colours and 4
-    depths with one 16-byte store each when the width is a multiple of 4 and
-    both buffers are 16-byte aligned, else pixel by pixel; output buffers only
-    4-byte aligned (offset by one element) give the same images."""
-    import torch
-
-    s = W.bulb_1080p(10, w, 40)
-    ref = gpu(api, s)
-    n = w * 40
-    big8 = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
-    bigd = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
-    out = {"rgba8": big8[1:1 + n].view(40, w), "depth": bigd[1:1 + n].view(40, w)}
-    api.render(s, out=out)
-    torch.cuda.synchronize()
-    assert np.array_equal(out["rgba8"].cpu().numpy(), ref["rgba8"])
-    assert np.array_equal(out["depth"].cpu().numpy(), ref["depth"])
-    # nothing written outside the views
-    assert int(big8[0]) == 0 and int(big8[n + 1]) == 0 and float(bigd[0]) == 0.0 and float(bigd[n + 1]) == 0.0
+    for r, g in zip(refs, got):
+        assert np.array_equal(r["rgba8"], g["rgba8"]) and np.array_equal(r["depth"], g["depth"])
