@@ -142,7 +142,8 @@ void orc_shade_d(const orc_scene *s, const double n[3], double vis, double rgba_
 void orc_shade_phong_d(const orc_scene *s, const double n[3], const double rd[3], double vis,
                        const double refl_rgb[3], double rgba_out[4]);
 /* unit normal at a point by the scene's normal mode (tetrahedral, central, or
- * -- Julia only -- analytic); rd is the fallback direction's ray */
+ * analytic: grad G / |grad G| of the Julia set or the Mandelbulb); rd is the
+ * fallback direction's ray */
 void orc_normal_scene_d(const orc_scene *s, const double p[3], const double rd[3], double n[3]);
 void orc_normal_scene_f(const orc_scene *s, const float p[3], const float rd[3], float n[3]);
 /* orbit-trap colour parameters of the DE at a point (see orc_outputs.trap) */

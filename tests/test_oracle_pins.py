@@ -688,3 +688,65 @@ def test_c_zero_julia_set_is_unit_ball(orc, p, mode):
         assert nrm @ (x / np.linalg.norm(x)) > 0.999, (idx, nrm)
         n_hit += 1
     assert n_hit > 300
+
+
+# ------------------------------------------- Mandelbulb: symmetry and analytic normal
+def _rot_y(theta):
+    c, s = math.cos(theta), math.sin(theta)
+    # the listing's azimuth a = atan2(x, z): a rotation about +y adds theta to a
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+@pytest.mark.parametrize("n", [8, 3, 5])
+def test_bulb_rotation_symmetry(orc, n):
+    """Eq. 1 multiplies the azimuth by n, so w -> w^n + c commutes with rotations
+    about the polar axis by 2 pi / (n - 1): the Mandelbulb, its DE and its analytic
+    normal are symmetric under them (the normal rotates with the point)."""
+    s = W.bulb_1080p(0, 8, 8)
+    s.update(n=n, normal_mode="analytic", max_iter=10)
+    rot = _rot_y(2 * math.pi / (n - 1))
+    rng = np.random.default_rng(14)
+    pts = rng.uniform(-1.2, 1.2, (300, 3))
+    d0, n0, _, _ = orc.de(s, pts)
+    d1, n1, _, _ = orc.de(s, pts @ rot.T)
+    same = n0 == n1
+    assert np.mean(same) > 0.98
+    assert np.allclose(d0[same], d1[same], rtol=1e-9, atol=1e-12)
+    for p in pts[same][:80]:
+        a = orc.normal_scene(s, p)
+        b = orc.normal_scene(s, rot @ p)
+        assert np.allclose(rot @ a, b, rtol=0, atol=1e-8), (p, rot @ a, b)
+
+
+@pytest.mark.parametrize("n", [8, 3])
+def test_bulb_analytic_normal_is_the_potential_gradient(orc, n):
+    """The analytic normal is the direction of grad log|w_N| (w_N the orbit's last
+    iterate): checked against central differences of log|w_N|^2 from the DE's own
+    orbit at points whose iteration count is the same at every tap.  (It is not
+    the direction of the DE's gradient: the Mandelbulb listing's DE carries a
+    scalar derivative, so its level sets tilt by a few degrees against the
+    potential's.)"""
+    s = W.bulb_1080p(0, 8, 8)
+    s.update(n=n, normal_mode="analytic", max_iter=12)
+    rng = np.random.default_rng(15)
+    dirs = rng.standard_normal((400, 3))
+    pts = dirs / np.linalg.norm(dirs, axis=1)[:, None] * rng.uniform(0.8, 1.4, (400, 1))
+    h = 1e-6
+    good = agree = 0
+    for p in pts:
+        d0, n0, tr0, m0 = orc.de(s, [p])
+        g = np.zeros(3)
+        ok = True
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = h
+            _, _, trp, mp = orc.de(s, [p + e])
+            _, _, trm, mm = orc.de(s, [p - e])
+            ok &= trp[0] == tr0[0] and trm[0] == tr0[0]
+            g[j] = (math.log(mp[0]) - math.log(mm[0])) / (2 * h)
+        if not ok or not np.all(np.isfinite(g)):
+            continue
+        good += 1
+        a = orc.normal_scene(s, p)
+        agree += (a @ g / np.linalg.norm(g)) > 1 - 1e-7
+    assert good > 200 and agree / good >= 0.99, (good, agree)
