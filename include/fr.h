@@ -156,7 +156,9 @@ typedef struct {
     int32_t max_steps;
     float eps;
     float max_step;
-    int32_t normal_mode;
+    int32_t normal_mode;     /* as for the Julia set; FR_NORMAL_ANALYTIC carries
+                                J = dw/dc through Eq. 1 (J <- DP(w) J + I) and
+                                takes grad G along J^T w_N                       */
     float normal_h;
     int32_t algebraic;       /* 0: the listing's acos/atan2/sin/cos power; 1: the same
                                 Eq. 1 by de Moivre powers of cos + i sin, no

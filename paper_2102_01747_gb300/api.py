@@ -16,6 +16,11 @@ def _f(vals, n):
     return (ctypes.c_float * n)(*[float(v) for v in vals])
 
 
+def _normal_mode(scene: dict) -> int:
+    return {"tetra": F.FR_NORMAL_TETRA, "central": F.FR_NORMAL_CENTRAL,
+            "analytic": F.FR_NORMAL_ANALYTIC}[scene["normal_mode"]]
+
+
 def julia_params(scene: dict) -> F.fr_julia_params:
     p = F.fr_julia_params()
     p.c = _f(scene["c"], 4)
@@ -27,8 +32,7 @@ def julia_params(scene: dict) -> F.fr_julia_params:
     p.max_steps = int(scene["max_steps"])
     p.eps = float(scene["eps"])
     p.max_step = float(scene["max_step"])
-    p.normal_mode = {"tetra": F.FR_NORMAL_TETRA, "central": F.FR_NORMAL_CENTRAL,
-                     "analytic": F.FR_NORMAL_ANALYTIC}[scene["normal_mode"]]
+    p.normal_mode = _normal_mode(scene)
     p.normal_h = float(scene["normal_h"])
     return p
 
@@ -42,7 +46,7 @@ def bulb_params(scene: dict) -> F.fr_bulb_params:
     p.max_steps = int(scene["max_steps"])
     p.eps = float(scene["eps"])
     p.max_step = float(scene["max_step"])
-    p.normal_mode = F.FR_NORMAL_TETRA if scene["normal_mode"] == "tetra" else F.FR_NORMAL_CENTRAL
+    p.normal_mode = _normal_mode(scene)
     p.normal_h = float(scene["normal_h"])
     p.algebraic = 1 if scene.get("algebraic") else 0
     return p

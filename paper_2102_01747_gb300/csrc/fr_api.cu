@@ -113,8 +113,6 @@ fr_status resolve_bulb(fr::DevReq &R, const fr_bulb_params *P)
     if (P->n < 2 || P->n > 16) return fail(FR_EINVAL, "mandelbulb power n=%d outside 2..16", P->n);
     if (!(P->bailout > 0.0f) || !std::isfinite(P->bailout))
         return fail(FR_EINVAL, "bailout must be positive and finite");
-    if (P->normal_mode == FR_NORMAL_ANALYTIC)
-        return fail(FR_EINVAL, "the analytic normal is implemented for the Julia set only");
     R.kind = FR_KIND_BULB;
     R.c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     R.power = P->n;

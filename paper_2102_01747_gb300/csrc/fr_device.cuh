@@ -595,6 +595,73 @@ __device__ __forceinline__ float3 finish_normal(float3 g, float3 rd)
     return v3(dvd(g.x, l), dvd(g.y, l), dvd(g.z, l));
 }
 
+// Analytic normal of the Mandelbulb: the construction of julia_analytic_normal
+// with G = lim log|w_N| / n^N and J = dw_N / dc.  c enters every step of Eq. 1,
+// so a column d of J follows d <- DP(w) d + e from d_0 = e (e the column's unit
+// vector), where DP is the Jacobian of the power
+// P(w) = r^n (sin b sin a, cos b, sin b cos a) in the listing's angles
+// (u = w.y / r, b = n acos u, a = n atan2(w.x, w.z)):
+//   dr = (w . d) / r,  du = (d.y r - w.y dr) / r^2,  db = -n du / sqrt(1 - u^2),
+//   da = n (w.z d.x - w.x d.z) / (w.x^2 + w.z^2),  d(r^n) = n r^(n-1) dr,
+// with db (da) taken as 0 on the polar axis where sqrt(1 - u^2) (w.x^2 + w.z^2)
+// vanishes.  Gradient component k = w_N . (column k); the orbit stops where the
+// DE's does.  The orbit runs once per column, each pass carrying one column:
+// all three columns in one pass held 16 more registers across the whole
+// one-ray-per-thread kernel (48 -> 64 for the Mandelbulb), a cost every pixel
+// pays, while three passes cost hit pixels three orbits, one fewer than the
+// tetrahedral stencil.  Each pass repeats the same operations on w, so the
+// orbit, its length and the stop are the same in all three.
+__device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, float3 x, float3 rd, int &trips)
+{
+    const int n = R.power;
+    const float nf = (float)n;
+    float3 g = v3(0.0f, 0.0f, 0.0f);
+    int i = 0;
+#pragma unroll 1
+    for (int col = 0; col < 3; col++) {
+        float3 w = x;
+        float3 d = v3(col == 0 ? 1.0f : 0.0f, col == 1 ? 1.0f : 0.0f, col == 2 ? 1.0f : 0.0f);
+        i = 0;
+        for (int k = 0; k < R.max_iter; k++) {
+            i++;
+            const float r = sqrtf(dot3(w, w));
+            float3 P = v3(0.0f, 0.0f, 0.0f), dP = P;
+            if (r > 0.0f) {
+                const float u = fminf(fmaxf(dvd(w.y, r), -1.0f), 1.0f);
+                const float b = mul(nf, acosf(u));
+                const float a = mul(nf, atan2f(w.x, w.z));
+                float sb, cb, sa, ca;
+                sincosf(b, &sb, &cb);
+                sincosf(a, &sa, &ca);
+                const float rn1 = rpow_nm1(r, n);
+                const float rn = mul(rn1, r);
+                P = v3(mul(rn, mul(sb, sa)), mul(rn, cb), mul(rn, mul(sb, ca)));
+                const float rho2 = fmaf(w.z, w.z, mul(w.x, w.x));
+                const float su = sqrtf(fmaxf(fmaf(-u, u, 1.0f), 0.0f));
+                const float dr = dvd(dot3(w, d), r);
+                const float du = dvd(fmaf(-w.y, dr, mul(d.y, r)), mul(r, r));
+                const float db = su > 0.0f ? dvd(mul(-nf, du), su) : 0.0f;
+                const float da = rho2 > 0.0f ? dvd(mul(nf, fmaf(w.z, d.x, -mul(w.x, d.z))), rho2) : 0.0f;
+                const float drn = mul(mul(nf, rn1), dr);
+                const float cbdb = mul(cb, db), sbda = mul(sb, da);
+                dP = v3(fmaf(drn, mul(sb, sa), mul(rn, fmaf(cbdb, sa, mul(ca, sbda)))),
+                        fmaf(drn, cb, -mul(rn, mul(sb, db))),
+                        fmaf(drn, mul(sb, ca), mul(rn, fmaf(cbdb, ca, -mul(sa, sbda)))));
+            }
+            d = v3(col == 0 ? add(dP.x, 1.0f) : dP.x, col == 1 ? add(dP.y, 1.0f) : dP.y,
+                   col == 2 ? add(dP.z, 1.0f) : dP.z);
+            w = v3(add(P.x, x.x), add(P.y, x.y), add(P.z, x.z));
+            if (dot3(w, w) > R.esc2) break;
+        }
+        const float gk = dot3(w, d);
+        if (col == 0) g.x = gk;
+        else if (col == 1) g.y = gk;
+        else g.z = gk;
+    }
+    trips = i;
+    return finish_normal(g, rd);
+}
+
 // shadow-ray origin x + off n
 __device__ __forceinline__ float3 offset_point(float3 x, float3 n, float off)
 {

@@ -338,9 +338,10 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
         after_normal<COUNT, PHONG>(S, R, pc);
         return;
     }
-    if (R.kind == 0 && R.normal_mode == 2) {  // analytic normal: one orbit with tangents, no stencil
+    if (R.normal_mode == 2) {  // analytic normal: one orbit with tangents, no stencil
         int trips;
-        S.g = julia_analytic_normal(R, S.x, S.rd, trips);
+        S.g = R.kind == 0 ? julia_analytic_normal(R, S.x, S.rd, trips)
+                          : bulb_analytic_normal(R, S.x, S.rd, trips);
         if (COUNT) {
             pc.v[kStatNormalDE] += 1;
             pc.v[kStatOrbit] += trips;

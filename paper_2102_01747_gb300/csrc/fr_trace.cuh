@@ -37,14 +37,16 @@ __device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, flo
 }
 
 // Normal = normalised gradient of the DE at x from the stencil taps of
-// tap_point / tap_accum (tetrahedral Eq. 5 or central differences); a zero or
-// non-finite gradient gives -rd.
+// tap_point / tap_accum (tetrahedral Eq. 5 or central differences), or the
+// analytic normal (one orbit carrying its Jacobian); a zero or non-finite
+// gradient gives -rd.
 template <int KIND, int U, bool COUNT>
 __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd, Counters &cnt)
 {
-    if (KIND == 0 && R.normal_mode == 2) {
+    if (R.normal_mode == 2) {
         int trips;
-        const float3 n = julia_analytic_normal(R, x, rd, trips);
+        const float3 n = KIND == 0 ? julia_analytic_normal(R, x, rd, trips)
+                                   : bulb_analytic_normal(R, x, rd, trips);
         if (COUNT) {
             cnt.v[kStatNormalDE] += 1;
             cnt.v[kStatOrbit] += trips;

@@ -141,6 +141,19 @@ def test_bad_bulb_arguments_refused(F, mutate, needle):
     assert st == F.FR_EINVAL and needle in msg, msg
 
 
+@pytest.mark.parametrize("mode", ["tetra", "central", "analytic"])
+def test_scene_normal_mode_reaches_both_param_structs(F, mode):
+    """The binding carries every normal mode into both fractals' parameter
+    blocks, and an unknown mode is an error rather than a silent default."""
+    from paper_2102_01747_gb300 import api
+
+    code = {"tetra": F.FR_NORMAL_TETRA, "central": F.FR_NORMAL_CENTRAL, "analytic": F.FR_NORMAL_ANALYTIC}[mode]
+    assert api.julia_params(dict(W.julia_256(8, 8), normal_mode=mode)).normal_mode == code
+    assert api.bulb_params(dict(W.bulb_1080p(0, 8, 8), normal_mode=mode)).normal_mode == code
+    with pytest.raises(KeyError):
+        api.bulb_params(dict(W.bulb_1080p(0, 8, 8), normal_mode="sobel"))
+
+
 def test_no_output_refused(F):
     st, msg = _call(F, W.julia_256(16, 16))
     assert st == F.FR_EINVAL and "no output" in msg

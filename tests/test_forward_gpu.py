@@ -248,7 +248,24 @@ def test_analytic_normal_render(api, orc, p):
     assert np.array_equal(b["rgba8"].cpu().numpy(), g["rgba8"])
 
 
-@pytest.mark.parametrize("case", ["bulb", "julia_cut", "julia_analytic", "bulb_jitter"])
+@pytest.mark.parametrize("n,alg", [(8, False), (8, True), (3, False), (5, False)])
+def test_bulb_analytic_normal_render(api, orc, n, alg):
+    """Mandelbulbs shaded with the analytic normal (J = dw/dc carried through
+    Eq. 1) against the oracle, and the batch call's image bit for bit."""
+    s = W.bulb_1080p(5, 200, 120)
+    s.update(n=n, algebraic=alg, normal_mode="analytic")
+    s["light"]["shadows"] = True
+    res, _, _ = check(api, orc, s)
+    assert res["hits"] > 3000
+    import torch
+
+    b = api.render_batch([s], rgba8=True, depth=True)[0]
+    torch.cuda.synchronize()
+    g = gpu(api, s)
+    assert np.array_equal(b["rgba8"].cpu().numpy(), g["rgba8"])
+
+
+@pytest.mark.parametrize("case", ["bulb", "julia_cut", "julia_analytic", "bulb_analytic", "bulb_jitter"])
 def test_phong_reflection_render(api, orc, case):
     """The Phong + Fresnel-weighted mirror-ray model against the oracle's."""
     if case == "bulb":
@@ -258,6 +275,8 @@ def test_phong_reflection_render(api, orc, case):
         s["light"]["shadows"] = True
     elif case == "julia_analytic":
         s = W.phong(dict(W.julia_256(128, 128), normal_mode="analytic"), k_specular=0.8, shininess=8.0)
+    elif case == "bulb_analytic":
+        s = W.phong(dict(W.bulb_1080p(8, 160, 96), normal_mode="analytic"), reflect_coef=0.7)
     else:
         s = W.phong(W.bulb_1080p(3, 96, 64), reflect_coef=1.0)
         s["camera"]["spp"], s["camera"]["seed"] = 3, 5
@@ -281,13 +300,17 @@ def test_phong_counters_match_oracle(api, orc):
 
 
 def test_phong_on_the_lane_kernel(api):
-    """The lane state machine (single_kernel 1) runs the mirror stage too and
-    gives the one-ray-per-thread kernel's images bit for bit."""
+    """The lane state machine (single_kernel 1) runs the mirror stage and the
+    Mandelbulb's analytic normal too and gives the one-ray-per-thread kernel's
+    images bit for bit."""
     from paper_2102_01747_gb300 import _ffi as F
 
     scenes = [W.phong(W.bulb_1080p(12, 120, 72)),
-              W.phong(dict(W.julia_256(96, 64), plane={"n": (0.2, 0.1, 1.0), "o": 0.1}), reflect_coef=0.6)]
+              W.phong(dict(W.julia_256(96, 64), plane={"n": (0.2, 0.1, 1.0), "o": 0.1}), reflect_coef=0.6),
+              dict(W.bulb_1080p(6, 120, 72), n=5, normal_mode="analytic"),
+              W.phong(dict(W.bulb_1080p(9, 120, 72), normal_mode="analytic"))]
     scenes[1]["light"]["shadows"] = True
+    scenes[2]["light"]["shadows"] = True
     refs = [gpu(api, s) for s in scenes]
     old = F.fr_get_tuning()
     t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])

@@ -31,7 +31,7 @@ def random_scene(rng):
         s["n"] = int(rng.integers(2, 17))
         s["bailout"] = float(rng.uniform(1.5, 3.0))
         s["algebraic"] = bool(rng.random() < 0.3)
-        s["normal_mode"] = str(rng.choice(["tetra", "central"]))
+        s["normal_mode"] = str(rng.choice(["tetra", "central", "analytic"]))
     s["max_iter"] = int(rng.integers(3, 16))
     s["max_steps"] = int(rng.integers(40, 300))
     s["eps"] = float(10 ** rng.uniform(-3.3, -2.3))
