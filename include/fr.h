@@ -282,13 +282,31 @@ FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, 
  * result does not depend on the order the GPU runs the pixels in: the same
  * inputs give the same gradient bits.  Calls that overlap on the GPU (on
  * different streams, or from different threads) share that accumulator and
- * race on it; serialise them.
+ * race on it; serialise them, or give each its own workspace through
+ * fr_render_backward_ws.
  * Errors: FR_EINVAL (spp != 1, Phong shading, NULL buffers, bad parameters),
  * FR_ECUDA. */
 FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,
                                     const fr_camera *camera, const fr_light *light,
                                     const float *saved, const float *d_rgba, const float *d_depth,
                                     float *grad, void *stream);
+
+/* fr_render_backward with the double accumulator in caller-owned device
+ * memory instead of the library's, so that calls with different workspaces
+ * may overlap on the GPU (different streams or threads; one workspace per call
+ * in flight).  The call clears the workspace on `stream` before its kernel and
+ * the kernel leaves it cleared; its contents between calls carry nothing.
+ *   workspace  device memory, 16-byte aligned, fr_backward_workspace_bytes()
+ *              bytes (11 doubles and a block counter)
+ * Same result bits as fr_render_backward for the same inputs.
+ * Errors: FR_EINVAL (workspace NULL or misaligned, and as fr_render_backward),
+ * FR_ENOMEM (ws_bytes too small), FR_ECUDA.  The workspace is checked before
+ * anything else. */
+FR_API size_t fr_backward_workspace_bytes(void);
+FR_API fr_status fr_render_backward_ws(const fr_julia_params *params, const fr_plane *plane,
+                                       const fr_camera *camera, const fr_light *light,
+                                       const float *saved, const float *d_rgba, const float *d_depth,
+                                       float *grad, void *workspace, size_t ws_bytes, void *stream);
 
 /* Read / replace the process-wide launch shapes (checked; FR_EINVAL if out of range). */
 FR_API fr_status fr_get_tuning(fr_tuning *out);

@@ -86,6 +86,11 @@ SIGNATURES = {
     "fr_render_backward": (c_int32, [ctypes.POINTER(fr_julia_params), ctypes.POINTER(fr_plane),
                                      ctypes.POINTER(fr_camera), ctypes.POINTER(fr_light), c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fr_backward_workspace_bytes": (ctypes.c_size_t, []),
+    "fr_render_backward_ws": (c_int32, [ctypes.POINTER(fr_julia_params), ctypes.POINTER(fr_plane),
+                                        ctypes.POINTER(fr_camera), ctypes.POINTER(fr_light), c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
+                                        c_void_p]),
     "fr_get_tuning": (c_int32, [ctypes.POINTER(fr_tuning)]),
     "fr_set_tuning": (c_int32, [ctypes.POINTER(fr_tuning)]),
     "fr_last_error": (ctypes.c_char_p, []),
@@ -159,6 +164,17 @@ def fr_render_backward(params, plane, camera, light, saved, d_rgba, d_depth, gra
     return load().fr_render_backward(ctypes.byref(params), ctypes.byref(plane) if plane else None,
                                      ctypes.byref(camera), ctypes.byref(light), saved, d_rgba,
                                      d_depth, grad, stream)
+
+
+def fr_backward_workspace_bytes():
+    return load().fr_backward_workspace_bytes()
+
+
+def fr_render_backward_ws(params, plane, camera, light, saved, d_rgba, d_depth, grad, workspace, ws_bytes,
+                          stream=None):
+    return load().fr_render_backward_ws(ctypes.byref(params), ctypes.byref(plane) if plane else None,
+                                        ctypes.byref(camera), ctypes.byref(light), saved, d_rgba,
+                                        d_depth, grad, workspace, int(ws_bytes), stream)
 
 
 def fr_get_tuning():

@@ -4,8 +4,9 @@
 
 rgba (H, W, 4) float32 and depth (H, W) float32 (+inf on a miss) come from
 fr_render_julia with the float colour and the saved hit state requested; the
-backward pass is fr_render_backward (implicit differentiation at the saved hit
-points, reverse mode through the recomputed orbit).  The differentiable inputs
+backward pass is fr_render_backward_ws (implicit differentiation at the saved
+hit points, reverse mode through the recomputed orbit) with a workspace of its
+own, so backward passes on different streams may overlap.  The differentiable inputs
 are 1-D tensors: c (4), plane_n (3), plane_o (1), light_dir (3).  Every other
 parameter is taken from `scene`.  Gradients with respect to the alpha channel
 are ignored (alpha is piecewise constant); so are depth cotangents on pixels
@@ -52,10 +53,12 @@ class JuliaRender(torch.autograd.Function):
         dd = None
         if d_depth is not None:
             dd = torch.nan_to_num(d_depth.float(), nan=0.0, posinf=0.0, neginf=0.0).contiguous()
-        st = F.fr_render_backward(api.julia_params(s), api.plane_struct(s), api.camera_struct(s),
-                                  api.light_struct(s), saved.data_ptr(), d_rgba.data_ptr(),
-                                  None if dd is None else dd.data_ptr(), grad.data_ptr(),
-                                  api.current_stream(ctx.dev))
+        ws = backward_workspace(ctx.dev)
+        st = F.fr_render_backward_ws(api.julia_params(s), api.plane_struct(s), api.camera_struct(s),
+                                     api.light_struct(s), saved.data_ptr(), d_rgba.data_ptr(),
+                                     None if dd is None else dd.data_ptr(), grad.data_ptr(),
+                                     ws.data_ptr(), ws.numel() * ws.element_size(),
+                                     api.current_stream(ctx.dev))
         F.check(st)
         dc, dn, do, dl = ctx.in_dev
         return grad[0:4].to(dc), grad[4:7].to(dn), grad[7:8].to(do), grad[8:11].to(dl), None
@@ -65,13 +68,25 @@ def julia_render(scene, c, plane_n, plane_o, light_dir):
     return JuliaRender.apply(c, plane_n, plane_o, light_dir, scene)
 
 
-def backward_raw(scene, saved, d_rgba, d_depth=None, grad=None):
-    """Direct call of fr_render_backward; returns the 11-vector (accumulated into grad)."""
+def backward_workspace(device) -> torch.Tensor:
+    """Device scratch for one fr_render_backward_ws call (16-byte aligned)."""
+    return torch.empty((int(F.fr_backward_workspace_bytes()) + 7) // 8, dtype=torch.float64, device=device)
+
+
+def backward_raw(scene, saved, d_rgba, d_depth=None, grad=None, workspace=None):
+    """Direct call of fr_render_backward (the library's accumulator) or, with a
+    workspace tensor, fr_render_backward_ws; returns the 11-vector
+    (accumulated into grad)."""
     if grad is None:
         grad = torch.zeros(11, dtype=torch.float32, device=saved.device)
-    st = F.fr_render_backward(api.julia_params(scene), api.plane_struct(scene), api.camera_struct(scene),
-                              api.light_struct(scene), saved.data_ptr(), d_rgba.data_ptr(),
-                              None if d_depth is None else d_depth.data_ptr(), grad.data_ptr(),
-                              api.current_stream(saved.device))
+    args = (api.julia_params(scene), api.plane_struct(scene), api.camera_struct(scene),
+            api.light_struct(scene), saved.data_ptr(), d_rgba.data_ptr(),
+            None if d_depth is None else d_depth.data_ptr(), grad.data_ptr())
+    stream = api.current_stream(saved.device)
+    if workspace is None:
+        st = F.fr_render_backward(*args, stream)
+    else:
+        st = F.fr_render_backward_ws(*args, workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                     stream)
     F.check(st)
     return grad

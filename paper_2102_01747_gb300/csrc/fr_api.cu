@@ -400,11 +400,11 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
     return FR_OK;
 }
 
-FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,
-                                    const fr_camera *camera, const fr_light *light, const float *saved,
-                                    const float *d_rgba, const float *d_depth, float *grad, void *stream)
+// checks and resolves the arguments of a backward call into A (acc/done left NULL)
+static fr_status resolve_backward(fr::BwdArgs &A, const fr_julia_params *params, const fr_plane *plane,
+                                  const fr_camera *camera, const fr_light *light, const float *saved,
+                                  const float *d_rgba, const float *d_depth, float *grad)
 {
-    fr::BwdArgs A;
     std::memset(&A, 0, sizeof A);
     fr_status st = resolve_julia(A.R, params);
     if (st != FR_OK) return st;
@@ -430,6 +430,43 @@ FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plan
     A.plane_norm = A.R.plane_on ? std::sqrt(plane->n[0] * plane->n[0] + plane->n[1] * plane->n[1] +
                                             plane->n[2] * plane->n[2])
                                 : 1.0f;
+    return FR_OK;
+}
+
+FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plane *plane,
+                                    const fr_camera *camera, const fr_light *light, const float *saved,
+                                    const float *d_rgba, const float *d_depth, float *grad, void *stream)
+{
+    fr::BwdArgs A;
+    const fr_status st = resolve_backward(A, params, plane, camera, light, saved, d_rgba, d_depth, grad);
+    if (st != FR_OK) return st;
+    return launched(fr::launch_backward(A, (cudaStream_t)stream));
+}
+
+// 11 doubles, then the finished-block count, padded to 128 bytes
+FR_API size_t fr_backward_workspace_bytes(void) { return 128; }
+
+FR_API fr_status fr_render_backward_ws(const fr_julia_params *params, const fr_plane *plane,
+                                       const fr_camera *camera, const fr_light *light, const float *saved,
+                                       const float *d_rgba, const float *d_depth, float *grad,
+                                       void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!workspace) return fail(FR_EINVAL, "workspace is NULL");
+    if (!aligned(workspace, 16)) return fail(FR_EINVAL, "workspace must be 16-byte aligned");
+    if (ws_bytes < fr_backward_workspace_bytes())
+        return fail(FR_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, fr_backward_workspace_bytes());
+    fr::BwdArgs A;
+    const fr_status st = resolve_backward(A, params, plane, camera, light, saved, d_rgba, d_depth, grad);
+    if (st != FR_OK) return st;
+    A.acc = static_cast<double *>(workspace);
+    A.done = reinterpret_cast<unsigned int *>(static_cast<char *>(workspace) + 11 * sizeof(double));
+    // the kernel leaves the workspace zeroed, but a workspace fresh from the
+    // allocator (or left by a failed launch) is cleared here, in stream order
+    const cudaError_t e = cudaMemsetAsync(workspace, 0, fr_backward_workspace_bytes(), (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the error state so later calls start clean
+        return launched(e);
+    }
     return launched(fr::launch_backward(A, (cudaStream_t)stream));
 }
 

@@ -187,8 +187,10 @@ __device__ void pixel_grad(const BwdArgs &A, int px, int py, float gsum[11])
     gsum[10] += act * (n.z - L.z * ndl) / A.light_norm;
 }
 
-// The per-call gradient accumulator of the device (11 doubles) and the count
-// of finished blocks; both return to zero at the end of every call.
+// The library's gradient accumulator (11 doubles) and count of finished
+// blocks, used by calls that bring no workspace; both return to zero at the
+// end of every call.  A call with a workspace uses the 11 doubles and the
+// count there instead.
 __device__ double g_bwd_acc[11];
 __device__ unsigned int g_bwd_done;
 
@@ -223,25 +225,27 @@ __global__ void __launch_bounds__(256) backward_kernel(const __grid_constant__ B
     // adds them to the caller's gradient and clears the accumulator for the
     // next call.  No block waits for another: the last one is the one whose
     // ticket completes the count (fence, then count).
+    double *acc = A.acc ? A.acc : g_bwd_acc;
+    unsigned int *done = A.acc ? A.done : &g_bwd_done;
     if (threadIdx.x < 11) {
         float v = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += part[w][threadIdx.x];
-        if (v != 0.0f) atomicAdd(g_bwd_acc + threadIdx.x, (double)v);
+        if (v != 0.0f) atomicAdd(acc + threadIdx.x, (double)v);
     }
     __threadfence();
     __syncthreads();
     __shared__ bool last;
-    if (threadIdx.x == 0) last = atomicAdd(&g_bwd_done, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (last) {
         __threadfence();
         if (threadIdx.x < 11) {
             // read and clear in one step
             const unsigned long long bits =
-                atomicExch(reinterpret_cast<unsigned long long *>(g_bwd_acc + threadIdx.x), 0ull);
+                atomicExch(reinterpret_cast<unsigned long long *>(acc + threadIdx.x), 0ull);
             A.grad[threadIdx.x] += (float)__longlong_as_double((long long)bits);
         }
-        if (threadIdx.x == 0) g_bwd_done = 0u;
+        if (threadIdx.x == 0) *done = 0u;
     }
 }
 

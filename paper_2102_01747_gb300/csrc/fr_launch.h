@@ -28,6 +28,8 @@ struct BwdArgs {
     const float4 *d_rgba;    // cotangent of the float colour
     const float *d_depth;    // cotangent of the depth, may be NULL
     float *grad;             // 11 floats, accumulated
+    double *acc;             // 11 double partial totals, zero on entry; NULL = the library's own
+    unsigned int *done;      // finished-block count, zero on entry (with acc)
     float light_norm;        // |light dir| as given (before normalisation)
     float plane_norm;        // |plane n| as given
 };

@@ -233,6 +233,28 @@ def test_backward_refuses_phong(F):
     assert st == F.FR_EINVAL and "Lambert" in F.fr_last_error(), F.fr_last_error()
 
 
+def test_backward_workspace_checked_first(F):
+    """fr_render_backward_ws checks its workspace before anything else; the
+    pointers below are never dereferenced because every call is refused on
+    the host."""
+    s = W.julia_256(16, 16)
+    p, pl, cam, li = _structs(s)
+    n = F.fr_backward_workspace_bytes()
+    assert n >= 11 * 8 + 4 and n % 16 == 0
+    st = F.fr_render_backward_ws(p, pl, cam, li, None, None, None, None, None, n, None)
+    assert st == F.FR_EINVAL and "workspace is NULL" in F.fr_last_error()
+    st = F.fr_render_backward_ws(p, pl, cam, li, None, None, None, None, 8, n, None)
+    assert st == F.FR_EINVAL and "aligned" in F.fr_last_error()
+    st = F.fr_render_backward_ws(p, pl, cam, li, None, None, None, None, 256, n - 16, None)
+    assert st == F.FR_ENOMEM
+    # a well-formed workspace, then the ordinary argument checks
+    ph = _structs(W.phong(s))
+    st = F.fr_render_backward_ws(*ph, None, None, None, None, 256, n, None)
+    assert st == F.FR_EINVAL and "Lambert" in F.fr_last_error(), F.fr_last_error()
+    st = F.fr_render_backward_ws(p, pl, cam, li, None, None, None, None, 256, n, None)
+    assert st == F.FR_EINVAL and "must be given" in F.fr_last_error(), F.fr_last_error()
+
+
 def test_c_client_compiles_against_the_header():
     """A plain C99 program (tests/c_client/render_request.c) compiles with
     -Wall -Wextra -Werror against include/fr.h and links against libfr.so."""

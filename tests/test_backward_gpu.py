@@ -210,3 +210,36 @@ def test_gradient_bits_are_reproducible(mods):
     autograd.backward_raw(s, out["saved"], d_rgba, d_depth, grad=acc)
     torch.cuda.synchronize()
     assert np.array_equal(acc.cpu().numpy(), (grads[0] + grads[0]).astype(np.float32))
+
+
+def test_workspace_backward_overlapping_streams(mods):
+    """fr_render_backward_ws: the same bits as the library-accumulator call,
+    and calls on four streams at once, each with its own workspace, give
+    every caller the serial result."""
+    torch, api, autograd = mods
+    s, _ = W.diff_julia(W.BASE_SEED, 256, 256)
+    out = api.render(s, rgba8=False, rgba=True, depth=True, saved=True)
+    rng = np.random.default_rng(5)
+    cots = [(torch.tensor(rng.standard_normal((256 * 256, 4)).astype(np.float32), device="cuda"),
+             torch.tensor(rng.standard_normal(256 * 256).astype(np.float32), device="cuda")) for _ in range(4)]
+    serial = []
+    for d_rgba, d_depth in cots:
+        g = autograd.backward_raw(s, out["saved"], d_rgba, d_depth)
+        torch.cuda.synchronize()
+        serial.append(g.cpu().numpy())
+    ws = [autograd.backward_workspace("cuda") for _ in range(4)]
+    g = autograd.backward_raw(s, out["saved"], *cots[0], workspace=ws[0])
+    torch.cuda.synchronize()
+    assert np.array_equal(g.cpu().numpy(), serial[0])
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    grads = [torch.zeros(11, dtype=torch.float32, device="cuda") for _ in range(4)]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for k in range(4):
+            with torch.cuda.stream(streams[k]):
+                autograd.backward_raw(s, out["saved"], *cots[k], grad=grads[k], workspace=ws[k])
+        torch.cuda.synchronize()
+        for k in range(4):
+            assert np.array_equal(grads[k].cpu().numpy(), serial[k]), (rep, k)
+            grads[k].zero_()
+        torch.cuda.synchronize()
