@@ -394,6 +394,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the current launch shape")
+    ap.add_argument("--tile-order", type=int, choices=(0, 1, 2), default=None,
+                    help="fix the tile order of the one-ray-per-thread kernels (0 rows, 1 columns, "
+                         "2 rows upward); the autotuner then keeps it")
     ap.add_argument("--batch-kernel", type=int, choices=[0, 1], default=None,
                     help="fix fr_render_batch's schedule (1 one-ray-per-thread kernel over all "
                          "tiles, 0 persistent kernel); the autotuner then keeps it")
@@ -424,9 +427,12 @@ def main():
 
     B.build()
     F.load()
-    if args.batch_kernel is not None:
+    if args.batch_kernel is not None or args.tile_order is not None:
         t = F.fr_get_tuning()
-        t.batch_kernel = args.batch_kernel
+        if args.batch_kernel is not None:
+            t.batch_kernel = args.batch_kernel
+        if args.tile_order is not None:
+            t.tile_order = args.tile_order
         F.check(F.fr_set_tuning(t))
     stream = api.current_stream(dev)
     tstream = torch.cuda.current_stream(dev)
@@ -445,7 +451,17 @@ def main():
         space = dict(autotune.SPACE)
         if args.batch_kernel is not None:
             del space["batch_kernel"]
+        if args.tile_order is not None:
+            del space["tile_order"]
         tuning = autotune.tune(scenes, reps=3, space=space)  # untimed search over the launch shape
+        tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"])}
+    elif args.path == "plain" and len(scenes) == 1 and not args.no_autotune:
+        from paper_2102_01747_gb300 import autotune
+
+        space = dict(autotune.SINGLE_SPACE)
+        if args.tile_order is not None:
+            del space["tile_order"]
+        tuning = autotune.tune_single(scenes[0], reps=5, space=space)  # untimed: block, unroll, tile order
         tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"])}
 
     counts = count_frame(api, torch, scenes)

@@ -197,7 +197,7 @@ typedef struct {
 
 /* Launch shapes; the autotuner writes them, every later call reads them. */
 typedef struct {
-    int32_t plain_block;         /* threads per block of the one-ray-per-thread kernel (32..1024, x32) */
+    int32_t plain_block;         /* threads per block of the one-ray-per-thread kernel (32..256, x32) */
     int32_t plain_unroll;        /* orbit-loop unroll depth: 1, 2 or 4                  */
     int32_t persist_block;       /* threads per block of the persistent kernel          */
     int32_t persist_ctas_per_sm; /* resident CTAs per SM; 0 = as many as fit            */
@@ -209,6 +209,12 @@ typedef struct {
                                     queue, 1 (default) one-ray-per-thread kernel over
                                     every tile of every request in one launch
                                     (plain_block threads)                              */
+    int32_t tile_order;          /* how the one-ray-per-thread kernels lay their 4 x 8
+                                    tiles, in launch order, over each image: 0 (default)
+                                    rows top to bottom, 1 columns left to right, 2 rows
+                                    bottom to top.  The hardware starts CTAs roughly in
+                                    index order, so this decides which part of the frame
+                                    runs first; images are the same bit for bit.      */
 } fr_tuning;
 
 /* Render one quaternion Julia image with the one-ray-per-thread kernel

@@ -1,15 +1,18 @@
-"""Autotuner for the batched path's schedule and launch shape (fr_tuning).
+"""Autotuner for the launch shapes and schedules of fr_tuning.
 
-The knobs are the ones fr_render_batch is sensitive to:
+For fr_render_batch (tune):
   batch_kernel       1 one-ray-per-thread kernel over all tiles, 0 persistent kernel
   plain_block        threads per CTA of the one-ray-per-thread batch kernel
+  tile_order         order of the tiles in the launch (rows, columns, rows upward)
   persist_block      threads per CTA of the persistent kernel (64, 128, 256)
   refill_threshold   idle lanes that trigger a warp refill (the compaction interval)
   persist_unroll     Julia orbit steps per scheduling round (the unroll depth)
+For one request through fr_render_julia / fr_render_mandelbulb (tune_single):
+  plain_block, plain_unroll (orbit-loop unroll depth) and tile_order.
 The search is coordinate descent from the current setting: each knob in turn is
 swept with the others fixed, each candidate timed with CUDA events (median of a
-few launches of fr_render_batch on the caller's scenes), and the best kept.  A
-knob of the schedule not in use is skipped.
+few calls on the caller's scenes), and the best kept.  A knob of the schedule
+not in use is skipped.  Every setting renders the same images bit for bit.
 Results are cached in a JSON file keyed by GPU name and workload key, so a
 later process applies them without searching again.
 """
@@ -26,9 +29,15 @@ from . import api
 SPACE = {
     "batch_kernel": (1, 0),
     "plain_block": (64, 128, 256),
+    "tile_order": (0, 1, 2),
     "persist_block": (64, 128, 256),
     "refill_threshold": (1, 2, 4, 8, 16),
     "persist_unroll": (2, 4, 8),
+}
+SINGLE_SPACE = {
+    "plain_block": (64, 128, 256),
+    "plain_unroll": (1, 2, 4),
+    "tile_order": (0, 1, 2),
 }
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 
@@ -45,10 +54,7 @@ def apply(cfg: dict) -> None:
     F.check(F.fr_set_tuning(t))
 
 
-def _time_batch(scenes, outs, ws, reps: int) -> float:
-    arr = api.request_array(scenes, outs)
-    stream = api.current_stream()
-    run = lambda: F.check(F.fr_render_batch(arr, len(scenes), ws.data_ptr(), ws.numel(), stream))  # noqa: E731
+def _median_ms(run, reps: int) -> float:
     run()
     torch.cuda.synchronize()
     times = []
@@ -64,6 +70,22 @@ def _time_batch(scenes, outs, ws, reps: int) -> float:
     return times[len(times) // 2]
 
 
+def _time_batch(scenes, outs, ws, reps: int) -> float:
+    arr = api.request_array(scenes, outs)
+    stream = api.current_stream()
+    return _median_ms(lambda: F.check(F.fr_render_batch(arr, len(scenes), ws.data_ptr(), ws.numel(), stream)),
+                      reps)
+
+
+def _time_single(scene, out, reps: int) -> float:
+    """One fr_render_julia / fr_render_mandelbulb call with prebuilt structs."""
+    fn = F.fr_render_julia if scene["kind"] == "julia" else F.fr_render_mandelbulb
+    prm = api.julia_params(scene) if scene["kind"] == "julia" else api.bulb_params(scene)
+    args = (prm, api.plane_struct(scene), api.camera_struct(scene), api.light_struct(scene),
+            api.image_struct(out), api.current_stream())
+    return _median_ms(lambda: F.check(fn(*args)), reps)
+
+
 PERSIST_KNOBS = ("persist_block", "persist_ctas_per_sm", "refill_threshold", "persist_unroll")
 
 
@@ -71,30 +93,43 @@ def _in_use(knob: str, cfg: dict) -> bool:
     """Whether `knob` changes what fr_render_batch launches under `cfg`."""
     if knob in PERSIST_KNOBS:
         return cfg.get("batch_kernel", 0) == 0
-    if knob == "plain_block":
+    if knob in ("plain_block", "tile_order"):
         return cfg.get("batch_kernel", 0) == 1
     return True
 
 
 def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=None) -> dict:
-    """Coordinate descent over `space`; returns {"config": ..., "ms": ..., "trials": [...]}
-    and leaves the best configuration applied."""
-    space = space or SPACE
+    """Coordinate descent over `space` for fr_render_batch on `scenes`; returns
+    {"config": ..., "ms": ..., "trials": [...]} and leaves the best
+    configuration applied."""
     outs = [api.alloc_image(s) for s in scenes]
     ws = api.workspace(len(scenes))
+    return _descent(lambda: _time_batch(scenes, outs, ws, reps), space or SPACE, _in_use, passes, log)
+
+
+def tune_single(scene, reps: int = 5, passes: int = 1, space: dict | None = None, log=None) -> dict:
+    """The same search for one request through the single-request kernel (the
+    nested-loop kernel, single_kernel 0, is the one tuned)."""
+    out = api.alloc_image(scene)
+    apply({"single_kernel": 0})
+    return _descent(lambda: _time_single(scene, out, reps), space or SINGLE_SPACE, lambda k, c: True, passes,
+                    log)
+
+
+def _descent(timer, space, in_use, passes, log) -> dict:
     best = current()
-    best_ms = _time_batch(scenes, outs, ws, reps)
+    best_ms = timer()
     trials = [dict(best, ms=best_ms)]
     for _ in range(passes):
         for knob, values in space.items():
-            if not _in_use(knob, best):
+            if not in_use(knob, best):
                 continue
             for v in values:
                 if v == best[knob]:
                     continue
                 cand = dict(best, **{knob: v})
                 apply(cand)
-                ms = _time_batch(scenes, outs, ws, reps)
+                ms = timer()
                 trials.append(dict(cand, ms=ms))
                 if log:
                     log("%s=%s: %.3f ms" % (knob, v, ms))

@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 1};
+fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 1, 0};
 
 fr_tuning tuning()
 {
@@ -234,7 +234,7 @@ fr_status set_error(fr_status st, const char *msg) { return fail(st, "%s", msg);
 
 extern "C" {
 
-FR_API int32_t fr_abi_version(void) { return 1; }
+FR_API int32_t fr_abi_version(void) { return 2; }
 
 FR_API const char *fr_last_error(void) { return g_err.c_str(); }
 
@@ -260,6 +260,7 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
         return fail(FR_EINVAL, "refill_threshold outside 1..32");
     if (t->single_kernel != 0 && t->single_kernel != 1) return fail(FR_EINVAL, "single_kernel must be 0 or 1");
     if (t->batch_kernel != 0 && t->batch_kernel != 1) return fail(FR_EINVAL, "batch_kernel must be 0 or 1");
+    if (t->tile_order < 0 || t->tile_order > 2) return fail(FR_EINVAL, "tile_order must be 0, 1 or 2");
     std::lock_guard<std::mutex> lk(g_tuning_mu);
     g_tuning = *t;
     return FR_OK;
@@ -280,7 +281,9 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
         return launched(fr::launch_lanes(A, tu.plain_block, tu.persist_unroll, count, R.shading != 0,
                                          (cudaStream_t)stream));
     }
-    return launched(fr::launch_plain(R, tu.plain_block, tu.plain_unroll, count, (cudaStream_t)stream));
+    fr::DevReq Q = R;
+    Q.tile_order = tu.tile_order;
+    return launched(fr::launch_plain(Q, tu.plain_block, tu.plain_unroll, count, (cudaStream_t)stream));
 }
 
 FR_API fr_status fr_render_julia(const fr_julia_params *params, const fr_plane *plane,
@@ -375,6 +378,7 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
             for (int i = 0; i < n; i++) {
                 A.reqs[i] = all[(size_t)order[(size_t)(first + i)]];
                 A.reqs[i].unit_begin = ctas;
+                A.reqs[i].tile_order = tu.tile_order;
                 ctas += ctas_of(A.reqs[i]);
             }
             A.total_units = ctas;

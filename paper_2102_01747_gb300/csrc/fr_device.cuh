@@ -73,7 +73,7 @@ struct __align__(16) DevReq {
     float refl_coef;          // weight of the reflected colour
     int shading;              // 0 Lambert, 1 Phong + reflection bounce
     int quad_store;           // rgba8 / depth rows may be written 4 pixels per 16-byte store
-    float pad2;
+    int tile_order;           // order of the tiles over the grid (fr_tuning.tile_order)
     float4 bg;
     uint32_t *rgba8;
     float4 *rgba;

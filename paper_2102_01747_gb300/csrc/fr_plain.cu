@@ -8,14 +8,36 @@
 
 namespace fr {
 
+// Pixel of `lane` in tile number `tile` of request R.  Tiles are numbered in
+// launch order (the hardware hands CTAs to SMs roughly in index order), laid
+// over the image by R.tile_order: 0 rows of tiles top to bottom, 1 columns of
+// tiles left to right, 2 rows bottom to top.  The grid is padded to whole
+// CTAs; the padding tiles land past the image's right or bottom edge in every
+// order, so their lanes fail the px < width, py < height test.
+__device__ __forceinline__ void tile_pixel(const DevReq &R, long long tile, int lane, int &px, int &py)
+{
+    const long long tiles_y = (R.height + kTileH - 1) / kTileH;
+    long long tx, ty;
+    if (R.tile_order == 1) {
+        tx = tile / tiles_y;
+        ty = tile % tiles_y;
+    } else {
+        tx = tile % R.tiles_x;
+        ty = tile / R.tiles_x;
+        if (R.tile_order == 2 && ty < tiles_y) ty = tiles_y - 1 - ty;
+    }
+    px = (int)tx * kTileW + (lane & (kTileW - 1));
+    py = (int)ty * kTileH + (lane / kTileW);
+}
+
 template <int KIND, int U, bool COUNT, bool PHONG>
 __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevReq R)
 {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long tile = gtid >> 5;
     const int lane = threadIdx.x & 31;
-    const int px = (int)(tile % R.tiles_x) * kTileW + (lane & (kTileW - 1));
-    const int py = (int)(tile / R.tiles_x) * kTileH + (lane / kTileW);
+    int px, py;
+    tile_pixel(R, tile, lane, px, py);
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
@@ -60,8 +82,8 @@ __global__ void __launch_bounds__(256) batch_plain_kernel(const __grid_constant_
     const DevReq &R = A.reqs[lo];
     const long long tile = (cta - R.unit_begin) * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    const int px = (int)(tile % R.tiles_x) * kTileW + (lane & (kTileW - 1));
-    const int py = (int)(tile / R.tiles_x) * kTileH + (lane / kTileW);
+    int px, py;
+    tile_pixel(R, tile, lane, px, py);
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;

@@ -41,7 +41,7 @@ def test_exports_every_declared_symbol(F):
     for n in names:
         assert hasattr(lib, n), n
         assert n in F.SIGNATURES, "binding lacks " + n
-    assert F.fr_abi_version() == 1
+    assert F.fr_abi_version() == 2
 
 
 def test_struct_layout_matches_header(F):
@@ -181,10 +181,15 @@ def test_tuning_roundtrip_and_checks(F):
     bad = F.fr_tuning(*old)
     bad.refill_threshold = 0
     assert F.fr_set_tuning(bad) == F.FR_EINVAL
+    for v in (-1, 3):
+        bad = F.fr_tuning(*old)
+        bad.tile_order = v
+        assert F.fr_set_tuning(bad) == F.FR_EINVAL and "tile_order" in F.fr_last_error()
     good = F.fr_tuning(*old)
     good.plain_block = 64
+    good.tile_order = 2
     assert F.fr_set_tuning(good) == F.FR_OK
-    assert F.fr_get_tuning().plain_block == 64
+    assert F.fr_get_tuning().plain_block == 64 and F.fr_get_tuning().tile_order == 2
     assert F.fr_set_tuning(F.fr_tuning(*old)) == F.FR_OK
 
 

@@ -26,8 +26,9 @@ def stable_mask(orc, scene):
     """Pixels whose state the float and double oracle renders agree on (oracle-only)."""
     a = orc.render(scene, precision="f64", threads=8)
     b = orc.render(scene, precision="f32", threads=8)
-    return (a["flags"] == b["flags"]) & (np.abs(np.nan_to_num(a["depth"] - b["depth"], nan=0.0)) <
-                                         10 * scene["eps"])
+    both_hit = np.isfinite(a["depth"]) & np.isfinite(b["depth"])
+    gap = np.abs(np.where(both_hit, a["depth"], 0.0) - np.where(both_hit, b["depth"], 0.0))
+    return (a["flags"] == b["flags"]) & (gap < 10 * scene["eps"])
 
 
 def well_conditioned(orc, scene, min_cos=0.1):

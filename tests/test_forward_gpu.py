@@ -100,9 +100,10 @@ def test_jittered_samples(api, orc):
     check(api, orc, s)
 
 
-@pytest.mark.parametrize("block,unroll,single", [(32, 1, 0), (64, 2, 0), (256, 4, 0), (128, 1, 0),
-                                                (128, 1, 1), (64, 2, 1), (256, 8, 1)])
-def test_launch_shapes_give_identical_images(api, block, unroll, single):
+@pytest.mark.parametrize("block,unroll,single,order", [(32, 1, 0, 0), (64, 2, 0, 0), (256, 4, 0, 0), (128, 1, 0, 0),
+                                                      (128, 1, 0, 1), (64, 2, 0, 2), (32, 4, 0, 1), (256, 1, 0, 2),
+                                                      (128, 1, 1, 0), (64, 2, 1, 0), (256, 8, 1, 0)])
+def test_launch_shapes_give_identical_images(api, block, unroll, single, order):
     from paper_2102_01747_gb300 import _ffi as F
 
     old = F.fr_get_tuning()
@@ -111,7 +112,7 @@ def test_launch_shapes_give_identical_images(api, block, unroll, single):
     j = W.julia_256(130, 70)
     ref = (gpu(api, s), gpu(api, j))
     t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
-    t.plain_block, t.single_kernel = block, single
+    t.plain_block, t.single_kernel, t.tile_order = block, single, order
     if single:
         t.persist_unroll = unroll  # the lane state machine's Julia steps per round
     else:
@@ -121,12 +122,36 @@ def test_launch_shapes_give_identical_images(api, block, unroll, single):
         for scene, r in zip((s, j), ref):
             g = gpu(api, scene)
             # every rounding step is explicit, so neither the block shape, the
-            # unroll depth nor the kernel (nested loops or lane state machine)
-            # can change a single bit
+            # unroll depth, the tile order nor the kernel (nested loops or lane
+            # state machine) can change a single bit
             assert np.array_equal(g["rgba8"], r["rgba8"])
             assert np.array_equal(g["depth"], r["depth"])
     finally:
         F.fr_set_tuning(keep)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_tile_orders_in_batch(api, order):
+    """The batch kernel under every tile order gives the single-request images
+    bit for bit, on requests whose sides are not multiples of the tile."""
+    import torch
+
+    from paper_2102_01747_gb300 import _ffi as F
+
+    scenes = [W.julia_256(130, 70), W.bulb_1080p(3, 61, 93), W.julia_256(8, 8), W.bulb_1080p(7, 257, 31)]
+    singles = [gpu(api, sc) for sc in scenes]
+    old = F.fr_get_tuning()
+    t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+    t.tile_order, t.batch_kernel = order, 1
+    assert F.fr_set_tuning(t) == F.FR_OK
+    try:
+        outs = api.render_batch(scenes, rgba8=True, depth=True)
+        torch.cuda.synchronize()
+    finally:
+        F.fr_set_tuning(old)
+    for r, o in zip(singles, outs):
+        assert np.array_equal(r["rgba8"], o["rgba8"].cpu().numpy())
+        assert np.array_equal(r["depth"], o["depth"].cpu().numpy())
 
 
 def test_saved_state_and_outputs(api, orc):
