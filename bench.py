@@ -70,6 +70,9 @@ def workload(name: str, rank: int = 0):
         return [W.stress_bulb_4k(60 + rank)], "Mandelbulb n=8 3840x2160 4 spp, iteration cap 12 (frame 60)"
     if name == "stress_julia_4k":
         return [W.stress_julia_4k()], "quaternion Julia 3840x2160 with shadow rays"
+    if name == "julia_4k_analytic":
+        return [dict(W.stress_julia_4k(), normal_mode="analytic")], (
+            "quaternion Julia 3840x2160 with shadow rays, analytic normal (Sec. 2) instead of central differences")
     if name == "diff_julia":
         s, start = W.diff_julia(W.BASE_SEED + rank)
         return [s], "differentiable Julia 512x512: forward with saved state + implicit-diff adjoint"
@@ -461,8 +464,9 @@ def main():
         space = dict(autotune.SINGLE_SPACE)
         if args.tile_order is not None:
             del space["tile_order"]
-        tuning = autotune.tune_single(scenes[0], reps=5, space=space)  # untimed: block, unroll, tile order
-        tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"])}
+        tuning = autotune.tune_single(scenes[0], space=space)  # untimed: block, unroll, tile order
+        tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"]),
+                  "trial_ms": [[{k: t[k] for k in space}, round(t["ms"], 4)] for t in tuning["trials"]]}
 
     counts = count_frame(api, torch, scenes)
     per_scene_iters = []
@@ -569,10 +573,12 @@ def main():
 
 
 def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step):
-    """Two more views of the same frame: (1) Eq. 1 evaluated without
+    """More views of the same frame: (1) Eq. 1 evaluated without
     transcendental calls (de Moivre powers; same image within the parity bar);
-    (2) eight consecutive frames of the camera orbit in one fr_render_batch call,
-    where one frame's slowest pixels overlap the other frames' work."""
+    (2) the analytic normal in place of the tetrahedral stencil; (3) with the
+    orbit-trap output; (4) eight consecutive frames of the camera orbit in one
+    fr_render_batch call, where one frame's slowest pixels overlap the other
+    frames' work."""
     out = {}
     alg = [dict(s, algebraic=True) for s in scenes]
     counts = count_frame(api, torch, alg)
@@ -583,6 +589,18 @@ def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step
     out["algebraic_power"] = {"path": "plain", "ms_per_frame": total / args.steps * 1e3,
                               "value": (counts[0] + counts[1] + counts[6]) * args.steps / total / 1e6,
                               "unit": "Mrays/s", "orbit_iters": counts[5]}
+    # the analytic normal (one orbit carrying its Jacobian per hit, in place of
+    # the four stencil DEs) and the orbit-trap output (one more DE per hit pixel)
+    for name, sc, oo in (("analytic_normal", [dict(s, normal_mode="analytic") for s in scenes], outs),
+                         ("orbit_trap", scenes, [api.alloc_image(s, trap=True) for s in scenes])):
+        c = count_frame(api, torch, sc)
+        step = Renderer(api, F, sc, oo, "plain", api.current_stream())
+        for _ in range(args.warmup):
+            step()
+        times, total, _ = time_steps(torch, step, args.steps, tstream, flush)
+        out[name] = {"path": "plain", "ms_per_frame": total / args.steps * 1e3,
+                     "value": (c[0] + c[1] + c[6]) * args.steps / total / 1e6, "unit": "Mrays/s",
+                     "orbit_iters": c[5]}
     frames = [W.bulb_1080p(10 + k) for k in range(8)]
     fouts = [api.alloc_image(f) for f in frames]
     fc = count_frame(api, torch, frames)

@@ -11,8 +11,10 @@ For one request through fr_render_julia / fr_render_mandelbulb (tune_single):
   plain_block, plain_unroll (orbit-loop unroll depth) and tile_order.
 The search is coordinate descent from the current setting: each knob in turn is
 swept with the others fixed, each candidate timed with CUDA events (median of a
-few calls on the caller's scenes), and the best kept.  A knob of the schedule
-not in use is skipped.  Every setting renders the same images bit for bit.
+few calls on the caller's scenes), and a candidate replaces the current
+setting only when it is faster by more than `margin` (1 %), so that timing noise
+does not move the setting.  A knob of the schedule not in use is skipped.
+Every setting renders the same images bit for bit.
 Results are cached in a JSON file keyed by GPU name and workload key, so a
 later process applies them without searching again.
 """
@@ -98,25 +100,27 @@ def _in_use(knob: str, cfg: dict) -> bool:
     return True
 
 
-def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=None) -> dict:
+def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=None,
+         margin: float = 0.01) -> dict:
     """Coordinate descent over `space` for fr_render_batch on `scenes`; returns
     {"config": ..., "ms": ..., "trials": [...]} and leaves the best
     configuration applied."""
     outs = [api.alloc_image(s) for s in scenes]
     ws = api.workspace(len(scenes))
-    return _descent(lambda: _time_batch(scenes, outs, ws, reps), space or SPACE, _in_use, passes, log)
+    return _descent(lambda: _time_batch(scenes, outs, ws, reps), space or SPACE, _in_use, passes, log, margin)
 
 
-def tune_single(scene, reps: int = 5, passes: int = 1, space: dict | None = None, log=None) -> dict:
+def tune_single(scene, reps: int = 9, passes: int = 1, space: dict | None = None, log=None,
+                margin: float = 0.01) -> dict:
     """The same search for one request through the single-request kernel (the
     nested-loop kernel, single_kernel 0, is the one tuned)."""
     out = api.alloc_image(scene)
     apply({"single_kernel": 0})
     return _descent(lambda: _time_single(scene, out, reps), space or SINGLE_SPACE, lambda k, c: True, passes,
-                    log)
+                    log, margin)
 
 
-def _descent(timer, space, in_use, passes, log) -> dict:
+def _descent(timer, space, in_use, passes, log, margin) -> dict:
     best = current()
     best_ms = timer()
     trials = [dict(best, ms=best_ms)]
@@ -133,7 +137,7 @@ def _descent(timer, space, in_use, passes, log) -> dict:
                 trials.append(dict(cand, ms=ms))
                 if log:
                     log("%s=%s: %.3f ms" % (knob, v, ms))
-                if ms < best_ms:
+                if ms < best_ms * (1.0 - margin):
                     best, best_ms = cand, ms
             apply(best)
     apply(best)

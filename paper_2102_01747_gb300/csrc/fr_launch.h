@@ -46,6 +46,9 @@ cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cud
 cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, int unroll, bool count,
                                bool phong, cudaStream_t s);
 
+// the single-request kernel compiled with the Mandelbulb's analytic normal (unroll 1)
+cudaError_t launch_plain_ban(const DevReq &R, int block, bool count, cudaStream_t s);
+
 // lane-state-machine forward kernel without the queue: one pixel per lane, all tiles launched
 cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, bool phong, cudaStream_t s);
 

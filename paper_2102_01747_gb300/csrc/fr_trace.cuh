@@ -39,11 +39,14 @@ __device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, flo
 // Normal = normalised gradient of the DE at x from the stencil taps of
 // tap_point / tap_accum (tetrahedral Eq. 5 or central differences), or the
 // analytic normal (one orbit carrying its Jacobian); a zero or non-finite
-// gradient gives -rd.
-template <int KIND, int U, bool COUNT>
+// gradient gives -rd.  The Mandelbulb's analytic normal is compiled only into
+// the BAN instantiations (requests that ask for it are launched there): its
+// orbit is a third inlined copy of the trig step, and carried in every kernel
+// it slowed the Phong frame by 7 % (instruction fetch).
+template <int KIND, int U, bool COUNT, bool BAN>
 __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd, Counters &cnt)
 {
-    if (R.normal_mode == 2) {
+    if ((KIND == 0 || BAN) && R.normal_mode == 2) {
         int trips;
         const float3 n = KIND == 0 ? julia_analytic_normal(R, x, rd, trips)
                                    : bulb_analytic_normal(R, x, rd, trips);
@@ -77,7 +80,7 @@ __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd
 // single call site for all DE evaluations (one loop whose trips pick the point
 // by phase) measured slower again (1.10 ms; Julia 256^2 0.149 against
 // 0.117 ms): its phase bookkeeping costs more than the smaller code saves.
-template <int KIND, int U, bool COUNT>
+template <int KIND, int U, bool COUNT, bool BAN>
 __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float3 rd, float &t_hit,
                                                uint32_t &flags, float3 &xhit, Counters &cnt)
 {
@@ -110,7 +113,7 @@ __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float
             n = v3(R.plane_hat);
             fl |= kFlagFace;
         } else {
-            n = normal_at<KIND, U, COUNT>(R, x, rd, cnt);
+            n = normal_at<KIND, U, COUNT, BAN>(R, x, rd, cnt);
         }
         if (!R.shadows) break;
         if (COUNT) cnt.v[kStatShadowRays] += 1;
@@ -131,7 +134,7 @@ __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float
 // by Fresnel-Schlick in shade_phong.  The two hits' normals share one stencil
 // call, so the DE is still inlined twice.  Kept apart from the Lambert-only
 // loop above, which holds fewer live values.
-template <int KIND, int U, bool COUNT>
+template <int KIND, int U, bool COUNT, bool BAN>
 __device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro, float3 rd, float &t_hit,
                                                      uint32_t &flags, float3 &xhit, Counters &cnt)
 {
@@ -166,7 +169,7 @@ __device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro,
             }
             const float3 xh = along(mro, mrd, t);
             const bool face = fp && steps == 1;
-            const float3 nh = face ? v3(R.plane_hat) : normal_at<KIND, U, COUNT>(R, xh, mrd, cnt);
+            const float3 nh = face ? v3(R.plane_hat) : normal_at<KIND, U, COUNT, BAN>(R, xh, mrd, cnt);
             if (pass == kReflect) {
                 refl = phong(R, nh, mrd, 1.0f);  // no shadow ray, no further bounce
                 break;
@@ -204,7 +207,7 @@ __device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro,
 // warp's quad store (store_rgba8_depth).  PHONG compiles the Phong +
 // mirror-ray path in (requests still choose it with R.shading); without it the
 // Lambert-only code keeps fewer registers.
-template <int KIND, int U, bool COUNT, bool PHONG>
+template <int KIND, int U, bool COUNT, bool PHONG, bool BAN = false>
 __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Counters &cnt, uint32_t &c8,
                                              float &depth)
 {
@@ -220,9 +223,9 @@ __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Co
         if (COUNT) cnt.v[kStatPrimaryRays] += 1;
         float4 c;
         if constexpr (PHONG)
-            c = trace_sample_phong<KIND, U, COUNT>(R, ro, rd, t, f, x, cnt);
+            c = trace_sample_phong<KIND, U, COUNT, BAN>(R, ro, rd, t, f, x, cnt);
         else
-            c = trace_sample<KIND, U, COUNT>(R, ro, rd, t, f, x, cnt);
+            c = trace_sample<KIND, U, COUNT, BAN>(R, ro, rd, t, f, x, cnt);
         acc4(acc, c);
         if ((f & kFlagHit) && t < dmin) {
             dmin = t;

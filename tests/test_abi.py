@@ -230,6 +230,38 @@ def test_autotune_skips_knobs_of_the_other_schedule():
     assert not autotune._in_use("plain_block", {"batch_kernel": 0})
 
 
+def test_autotune_descent_switches_only_beyond_the_margin(F):
+    """Coordinate descent on a synthetic cost table (no GPU): a candidate
+    replaces the setting only when it is more than 1 % faster, and the search
+    leaves its choice applied through fr_set_tuning."""
+    from paper_2102_01747_gb300 import autotune
+
+    old = F.fr_get_tuning()
+    keep = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+    cost = {("plain_block", 64): 0.995, ("plain_block", 256): 0.90, ("tile_order", 1): 0.985,
+            ("tile_order", 2): 1.2}
+    try:
+        autotune.apply({"plain_block": 128, "tile_order": 0})
+
+        def timer():
+            cur = autotune.current()
+            ms = 1.0
+            for (k, v), f in cost.items():
+                if cur[k] == v:
+                    ms *= f
+            return ms
+
+        res = autotune._descent(timer, {"plain_block": (64, 128, 256), "tile_order": (0, 1, 2)},
+                                lambda k, c: True, 1, None, 0.01)
+        # 64 (0.5 % faster) is not taken, 256 (10 %) is; then column order (1.5 %) is
+        assert res["config"]["plain_block"] == 256 and res["config"]["tile_order"] == 1
+        assert abs(res["ms"] - 0.90 * 0.985) < 1e-12
+        t = F.fr_get_tuning()
+        assert t.plain_block == 256 and t.tile_order == 1
+    finally:
+        F.fr_set_tuning(keep)
+
+
 def test_backward_refuses_phong(F):
     """The adjoint covers Lambert shading; every buffer is NULL, so nothing could launch."""
     s = W.phong(W.julia_256(16, 16))

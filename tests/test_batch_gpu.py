@@ -204,7 +204,8 @@ def test_autotune_keeps_images_and_applies_its_choice(api):
                                                    "refill_threshold": (4, 16)})
         cur = autotune.current()
         assert all(cur[k] == v for k, v in res["config"].items())
-        assert len(res["trials"]) >= 2 and res["ms"] == min(t["ms"] for t in res["trials"])
+        # the kept setting is within the switching margin (1 %) of the fastest trial
+        assert len(res["trials"]) >= 2 and res["ms"] * (1 - 0.01) <= min(t["ms"] for t in res["trials"]) + 1e-9
         got = _np(api.render_batch(scenes, rgba8=True, depth=True))
     finally:
         F.fr_set_tuning(old)
