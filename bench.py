@@ -41,7 +41,7 @@ FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5, ("bulb", 8): 170.8}
 # DRAM bytes of one launch of the dominant kernel, from the ncu capture of the
 # same command (dram__bytes_read.sum + dram__bytes_write.sum); the frame's
 # 16.6 MB of stores are still in the 129 MB L2 when the kernel ends.
-TRAFFIC = {("bulb_1080p", "plain"): 1714176 + 3757568}
+TRAFFIC = {("bulb_1080p", "plain"): 1707264 + 1661696}
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32)
 
 

@@ -57,12 +57,15 @@ def test_batch_mixed_full_size(api, orc):
     assert hits > 10000
 
 
-@pytest.mark.parametrize("name", ["stress_bulb_4k", "stress_julia_4k", "bulb_1080p_phong"])
+@pytest.mark.parametrize("name", ["stress_bulb_4k", "stress_julia_4k", "bulb_1080p_phong", "julia_4k_analytic",
+                                  "bulb_1080p_analytic"])
 def test_single_request_full_size(api, orc, name):
     import torch
 
     s = {"stress_bulb_4k": lambda: W.stress_bulb_4k(60), "stress_julia_4k": W.stress_julia_4k,
-         "bulb_1080p_phong": lambda: W.phong(W.bulb_1080p(10))}[name]()
+         "bulb_1080p_phong": lambda: W.phong(W.bulb_1080p(10)),
+         "julia_4k_analytic": lambda: dict(W.stress_julia_4k(), normal_mode="analytic"),
+         "bulb_1080p_analytic": lambda: dict(W.bulb_1080p(10), normal_mode="analytic")}[name]()
     out = api.render(s, rgba8=True, depth=True)
     torch.cuda.synchronize()
     res = _check_sampled(out, s, _sample(s, 20000, 7), orc)
