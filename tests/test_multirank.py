@@ -4,8 +4,6 @@ collective) and the job time is the maximum over ranks."""
 import os
 import socket
 
-import pytest
-
 
 def _free_port():
     with socket.socket() as s:
