@@ -81,3 +81,28 @@ def test_stress_animation_frames(api, orc):
         out = api.render(s, rgba8=True, depth=True)
         torch.cuda.synchronize()
         _check_sampled(out, s, _sample(s, 6000, k), orc)
+
+
+@pytest.mark.parametrize("name", ["stress_julia_4k", "stress_bulb_4k"])
+def test_tile_orders_bitwise_at_full_size(api, name):
+    """The tile order the autotuner picks for the 4K workloads (columns) gives
+    the row-order image bit for bit at full size."""
+    import torch
+
+    from paper_2102_01747_gb300 import _ffi as F
+
+    s = W.stress_julia_4k() if name == "stress_julia_4k" else W.stress_bulb_4k(60)
+    old = F.fr_get_tuning()
+    imgs = []
+    try:
+        for order in (0, 1, 2):
+            t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+            t.tile_order, t.single_kernel = order, 0
+            assert F.fr_set_tuning(t) == F.FR_OK
+            out = api.render(s, rgba8=True, depth=True)
+            torch.cuda.synchronize()
+            imgs.append(out)
+    finally:
+        F.fr_set_tuning(old)
+    for o in imgs[1:]:
+        assert torch.equal(o["rgba8"], imgs[0]["rgba8"]) and torch.equal(o["depth"], imgs[0]["depth"])
