@@ -177,8 +177,11 @@ def test_saved_state_and_outputs(api, orc):
     assert np.all(np.abs(np.floor(np.clip(rgba, 0, 1) * 255 + 0.5) - q) <= 1)
 
 
-def test_stats_counters_match_oracle(api, orc):
-    s = W.bulb_1080p(10, 160, 90)
+@pytest.mark.parametrize("normal", ["tetra", "analytic"])
+def test_stats_counters_match_oracle(api, orc, normal):
+    """Work counters against the oracle's (the analytic normal counts one
+    normal evaluation and one orbit per hit)."""
+    s = dict(W.bulb_1080p(10, 160, 90), normal_mode=normal)
     out = api.render(s, stats=True)
     import torch
 
