@@ -75,10 +75,14 @@ def implicit_per_pixel(orc, scene, d_rgba, d_depth, idx):
     return out
 
 
-def test_implicit_gradient_matches_fd_per_pixel(orc):
+@pytest.mark.parametrize("normal", ["central", "analytic"])
+def test_implicit_gradient_matches_fd_per_pixel(orc, normal):
+    """Per pixel at a converged march; the analytic normal (Sec. 2) moves
+    through c and the hit point inside its own orbit, differentiated on dual
+    numbers, against the finite differences of the rendered colour."""
     size = 40
     s, _ = W.diff_julia(W.BASE_SEED, size, size)
-    s["eps"], s["max_steps"] = 1e-9, 5000
+    s["eps"], s["max_steps"], s["normal_mode"] = 1e-9, 5000, normal
     d_rgba, d_depth = cotangents(size * size)
     fd, mask, base = fd_per_pixel(orc, s, d_rgba, d_depth, 1e-6)
     for kind, sel in (("surface", base["flags"] == 1), ("face", (base["flags"] & 2) > 0)):
