@@ -141,8 +141,7 @@ typedef struct {
     float max_step;          /* step clamp (listing: 0.2), > 0                    */
     int32_t normal_mode;     /* FR_NORMAL_TETRA, FR_NORMAL_CENTRAL, or FR_NORMAL_ANALYTIC:
                                 grad d = grad G / |grad G| on the set (Sec. 2), from the
-                                orbit's derivative carried alongside it (no stencil;
-                                not accepted by fr_render_backward)                 */
+                                orbit's derivative carried alongside it (no stencil) */
     float normal_h;          /* stencil size; 0 = 0.5773*eps (tetra), 1e-4 (central) */
 } fr_julia_params;
 
@@ -272,7 +271,9 @@ FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, 
 /* Vector-Jacobian product of a Julia render (spp = 1) by implicit
  * differentiation at the hit point: for surface hits
  *     dt/dtheta = -(dd/dtheta) / (grad_x d . rd),
- * the normal's dependence through the stencil taps, Lambert's through n and L;
+ * the normal's dependence through the stencil taps (or, for the analytic
+ * normal, through J^T z_N by reverse mode over the orbit and its tangent),
+ * Lambert's through n and L;
  * cut-face hits through t = (offset - n.ro)/(n.rd) and the normal n/|n|.
  * The orbit is recomputed from the hit point saved by the forward call (same
  * parameters, out.saved given).  Escape counts, hit status and shadow

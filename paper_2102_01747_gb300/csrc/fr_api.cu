@@ -412,8 +412,6 @@ static fr_status resolve_backward(fr::BwdArgs &A, const fr_julia_params *params,
     std::memset(&A, 0, sizeof A);
     fr_status st = resolve_julia(A.R, params);
     if (st != FR_OK) return st;
-    if (params->normal_mode == FR_NORMAL_ANALYTIC)
-        return fail(FR_EINVAL, "backward supports the tetrahedral and central normals");
     if (light && light->shading != FR_SHADE_LAMBERT)
         return fail(FR_EINVAL, "backward supports Lambert shading");
     if (params->max_iter > fr::kMaxBwdIter)

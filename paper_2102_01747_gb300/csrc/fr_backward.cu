@@ -8,6 +8,8 @@
 //     dt/dtheta = -(dd/dtheta) / (grad_x d . rd)          (implicit function)
 // The normal is the normalised stencil sum g = sum_k w_k d(x + o_k) of the
 // forward pass; it moves through each tap's own dependence on c and through x.
+// The analytic normal's g = J^T z_N (Sec. 2) moves through c and x inside its
+// own orbit (julia_normal_vjp).
 // Lambert shading moves through n and through L = dir/|dir|.  A cut-face hit
 // sits on the plane: t = (o - n.ro)/(n.rd), normal n/|n|.
 //
@@ -93,6 +95,71 @@ __device__ float julia_de_grad(const DevReq &R, float3 p, float3 &gx, float4 &gc
     return d;
 }
 
+// transpose of z -> D(z^3)[t] (the tangent map of the cube, differentiated in
+// z with t fixed), applied to b.  With z = (a, v), t = (ta, tv):
+//   D(z^3)[t] = (3(a^2 - |v|^2) ta - 6a v.tv,  s v + f tv),
+//   s = 6a ta - 2 v.tv,  f = 3a^2 - |v|^2.
+__device__ __forceinline__ float4 jt_dcube(float4 z, float4 t, float4 b)
+{
+    const float a = z.x, ta = t.x;
+    const float vdt = z.y * t.y + z.z * t.z + z.w * t.w;
+    const float vdb = z.y * b.y + z.z * b.z + z.w * b.w;
+    const float tdb = t.y * b.y + t.z * b.z + t.w * b.w;
+    const float s = 6.0f * a * ta - 2.0f * vdt;
+    const float ab = b.x * (6.0f * a * ta - 6.0f * vdt) + 6.0f * ta * vdb + 6.0f * a * tdb;
+    const float cv = -6.0f * ta * b.x - 2.0f * tdb;  // coefficient of v
+    const float ct = -6.0f * a * b.x - 2.0f * vdb;   // coefficient of tv
+    return make_float4(ab, cv * z.y + ct * t.y + s * b.y, cv * z.z + ct * t.z + s * b.z,
+                       cv * z.w + ct * t.w + s * b.w);
+}
+
+// phi = z_N . tau_N, tau the orbit's tangent along u (tau_0 = (u, 0)): the
+// analytic normal's g (Sec. 2, julia_analytic_grad) contracted with u.
+// Returns d phi / d x (the slice's three directions) and d phi / d c by
+// reverse mode through the pair recursion (z, tau) -> (z^p + c, D(z^p)[tau]),
+// the orbit recomputed with the forward pass's step functions.
+template <int P>
+__device__ void julia_normal_vjp(const DevReq &R, float3 x, float3 u, float3 &gx, float4 &gc)
+{
+    float4 zs[kMaxBwdIter], ts[kMaxBwdIter];
+    Orbit o;
+    julia_init(o, x, R.slice_w);
+    float4 tau = make_float4(u.x, u.y, u.z, 0.0f);
+    int n = 0;
+    for (int k = 0; k < R.max_iter; k++) {
+        zs[k] = make_float4(o.a, o.b, o.c, o.d);
+        ts[k] = tau;
+        tangent_step(tau, o, P);
+        if (P == 2)
+            julia2_step(o, R.c);
+        else
+            julia3_step(o, R.c);
+        n++;
+        if (o.m > R.esc2) break;
+    }
+    float4 zb = tau;                                   // d phi / d z_N
+    float4 tb = make_float4(o.a, o.b, o.c, o.d);       // d phi / d tau_N
+    float4 cb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int k = n - 1; k >= 0; k--) {
+        cb.x += zb.x;
+        cb.y += zb.y;
+        cb.z += zb.z;
+        cb.w += zb.w;
+        const float4 z = zs[k], t = ts[k];
+        float4 nzb = (P == 2) ? jt_square(z, zb) : jt_cube(z, zb);
+        // D(z^2)[t] = z t + t z is symmetric in (z, t), so its z-derivative is the square's at t
+        const float4 dz = (P == 2) ? jt_square(t, tb) : jt_dcube(z, t, tb);
+        nzb.x += dz.x;
+        nzb.y += dz.y;
+        nzb.z += dz.z;
+        nzb.w += dz.w;
+        tb = (P == 2) ? jt_square(z, tb) : jt_cube(z, tb);
+        zb = nzb;
+    }
+    gx = v3(zb.x, zb.y, zb.z);
+    gc = cb;
+}
+
 // weight vector of stencil tap k in g = sum_k w_k d_k (see tap_accum)
 __device__ __forceinline__ float3 tap_weight(int mode, float h, int k)
 {
@@ -144,10 +211,15 @@ __device__ void pixel_grad(const BwdArgs &A, int px, int py, float gsum[11])
     const float srd = dot3(gx0, rd);
     const float4 dtdc = make_float4(-gc0.x / srd, -gc0.y / srd, -gc0.z / srd, -gc0.w / srd);
 
-    const int taps = R.normal_mode == 0 ? 4 : 6;
+    const bool analytic = R.normal_mode == 2;
+    const int taps = analytic ? 0 : (R.normal_mode == 0 ? 4 : 6);
     float grd[6];
     float4 gck[6];
     float3 g = v3(0.0f, 0.0f, 0.0f);
+    if (analytic) {
+        int trips;
+        g = julia_analytic_grad(R, x, trips);
+    }
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         if (k < taps) {
@@ -167,6 +239,12 @@ __device__ void pixel_grad(const BwdArgs &A, int px, int py, float gsum[11])
                         act * (L.z - n.z * ndl) / gl);
     float s = gd;  // coefficient of dt/dc
     float4 gcsum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (analytic) {
+        // g = J^T z_N moves through c and through x:  u . dg = d(g . u)
+        float3 gxu;
+        julia_normal_vjp<P>(R, x, u, gxu, gcsum);
+        s += dot3(gxu, rd);
+    }
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         if (k < taps) {

@@ -521,7 +521,8 @@ __device__ __forceinline__ void tangent_step(float4 &t, const Orbit &o, int p)
     t.x = na;
 }
 
-__device__ __forceinline__ float3 julia_analytic_normal(const DevReq &R, float3 x, float3 rd, int &trips)
+// g = (z_N . t_x, z_N . t_y, z_N . t_z), not normalised (the adjoint needs |g|)
+__device__ __forceinline__ float3 julia_analytic_grad(const DevReq &R, float3 x, int &trips)
 {
     Orbit o;
     julia_init(o, x, R.slice_w);
@@ -541,9 +542,14 @@ __device__ __forceinline__ float3 julia_analytic_normal(const DevReq &R, float3 
         if (o.m > R.esc2) break;
     }
     trips = i;
-    const float3 g = v3(fmaf(o.d, tx.w, fmaf(o.c, tx.z, fmaf(o.b, tx.y, mul(o.a, tx.x)))),
-                        fmaf(o.d, ty.w, fmaf(o.c, ty.z, fmaf(o.b, ty.y, mul(o.a, ty.x)))),
-                        fmaf(o.d, tz.w, fmaf(o.c, tz.z, fmaf(o.b, tz.y, mul(o.a, tz.x)))));
+    return v3(fmaf(o.d, tx.w, fmaf(o.c, tx.z, fmaf(o.b, tx.y, mul(o.a, tx.x)))),
+              fmaf(o.d, ty.w, fmaf(o.c, ty.z, fmaf(o.b, ty.y, mul(o.a, ty.x)))),
+              fmaf(o.d, tz.w, fmaf(o.c, tz.z, fmaf(o.b, tz.y, mul(o.a, tz.x)))));
+}
+
+__device__ __forceinline__ float3 julia_analytic_normal(const DevReq &R, float3 x, float3 rd, int &trips)
+{
+    const float3 g = julia_analytic_grad(R, x, trips);
     const float l = sqrtf(dot3(g, g));
     if (!(l > 0.0f) || !isfinite(l)) return v3(-rd.x, -rd.y, -rd.z);
     return v3(dvd(g.x, l), dvd(g.y, l), dvd(g.z, l));

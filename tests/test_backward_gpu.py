@@ -57,7 +57,8 @@ def gpu_grad(mods, scene, d_rgba, d_depth):
 
 # (the tetrahedral stencil's h = 0.5773 eps is too small for float at eps = 1e-5,
 # so it is compared at the workload eps)
-@pytest.mark.parametrize("eps,normal", [(1e-5, "central"), (1e-3, "tetra"), (1e-3, "central")])
+@pytest.mark.parametrize("eps,normal", [(1e-5, "central"), (1e-3, "tetra"), (1e-3, "central"),
+                                        (1e-5, "analytic"), (1e-3, "analytic")])
 def test_gpu_adjoint_matches_fp64_reference(mods, orc, eps, normal):
     s, _ = W.diff_julia(W.BASE_SEED, 128, 128)
     s["eps"], s["max_steps"], s["normal_mode"] = eps, 2000, normal
@@ -79,7 +80,8 @@ def test_gpu_adjoint_matches_fp64_reference(mods, orc, eps, normal):
     assert np.linalg.norm(g[8:] - ref[8:]) <= tol * np.linalg.norm(ref[8:]) + 1e-6
 
 
-@pytest.mark.parametrize("variant", ["cube", "shadowed", "no_cut", "jittered_camera"])
+@pytest.mark.parametrize("variant", ["cube", "shadowed", "no_cut", "jittered_camera", "cube_analytic",
+                                     "no_cut_analytic"])
 def test_gpu_adjoint_variants(mods, orc, variant):
     """The adjoint beyond the workload's setting: the listing's degree 3, shadow
     rays (visibility held fixed), no cut plane, another camera.  The degree-3
@@ -89,12 +91,14 @@ def test_gpu_adjoint_variants(mods, orc, variant):
     (silhouettes, where the implicit derivative divides by a vanishing
     grad d . rd) are left out of the cotangents."""
     s, _ = W.diff_julia(W.BASE_SEED, 112, 96)
-    s["eps"], s["max_steps"] = (1e-3 if variant == "cube" else 1e-5), 2000
-    if variant == "cube":
+    s["eps"], s["max_steps"] = (1e-3 if variant.startswith("cube") else 1e-5), 2000
+    if variant.endswith("analytic"):
+        s["normal_mode"] = "analytic"
+    if variant.startswith("cube"):
         s.update(p=3, escape_r2=256.0, max_iter=12, c=(-0.1, 0.55, 0.3, 0.1))
     elif variant == "shadowed":
         s["light"]["shadows"] = True
-    elif variant == "no_cut":
+    elif variant.startswith("no_cut"):
         s["plane"] = None
     else:
         s["camera"]["eye"] = (-1.1, 0.4, 2.6)
@@ -119,9 +123,9 @@ def test_gpu_adjoint_variants(mods, orc, variant):
     # without the cut every hit lies on the fractal surface, where the float
     # reverse sweep through the orbit loses more digits than on the workload's
     # cut face (measured: 4 % apart, cosine 0.9993)
-    tol = 5e-2 if variant == "no_cut" else 2e-2
+    tol = 5e-2 if variant.startswith("no_cut") else 2e-2
     assert cos >= 1 - tol**2 and rel <= tol, (variant, g, ref, cos, rel)
-    if variant == "no_cut":
+    if variant.startswith("no_cut"):
         assert np.all(g[4:8] == 0.0) and np.all(ref[4:8] == 0.0)
 
 
