@@ -38,10 +38,11 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # is the degree-2 one scaled by the ratio of their orbit-step arithmetic
 # (28 / 24); other Mandelbulb powers take the n = 8 figure (same calls per step).
 FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5, ("bulb", 8): 170.8}
-# DRAM bytes of one launch of the dominant kernel, from the ncu capture of the
-# same command (dram__bytes_read.sum + dram__bytes_write.sum); the frame's
-# 16.6 MB of stores are still in the 129 MB L2 when the kernel ends.
-TRAFFIC = {("bulb_1080p", "plain"): 1707264 + 1661696}
+# DRAM bytes of one launch of the dominant kernel (by the kernel the tuned
+# configuration launches), from the ncu capture of the same command
+# (dram__bytes_read.sum + dram__bytes_write.sum); the frame's 16.6 MB of
+# stores are still in the 129 MB L2 when the kernel ends.
+TRAFFIC = {("bulb_1080p", "plain_kernel"): 1707264 + 1661696, ("bulb_1080p", "batch_plain_kernel"): 82176 + 3328}
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32)
 
 
@@ -397,6 +398,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the current launch shape")
+    ap.add_argument("--single-kernel", type=int, choices=(0, 1, 2), default=None,
+                    help="fix the kernel of fr_render_julia / fr_render_mandelbulb (0 single-request "
+                         "kernel, 1 lane state machine, 2 batch kernel); the autotuner then keeps it")
     ap.add_argument("--tile-order", type=int, choices=(0, 1, 2), default=None,
                     help="fix the tile order of the one-ray-per-thread kernels (0 rows, 1 columns, "
                          "2 rows upward); the autotuner then keeps it")
@@ -430,10 +434,12 @@ def main():
 
     B.build()
     F.load()
-    if args.batch_kernel is not None or args.tile_order is not None:
+    if args.batch_kernel is not None or args.tile_order is not None or args.single_kernel is not None:
         t = F.fr_get_tuning()
         if args.batch_kernel is not None:
             t.batch_kernel = args.batch_kernel
+        if args.single_kernel is not None:
+            t.single_kernel = args.single_kernel
         if args.tile_order is not None:
             t.tile_order = args.tile_order
         F.check(F.fr_set_tuning(t))
@@ -464,7 +470,9 @@ def main():
         space = dict(autotune.SINGLE_SPACE)
         if args.tile_order is not None:
             del space["tile_order"]
-        tuning = autotune.tune_single(scenes[0], space=space)  # untimed: block, unroll, tile order
+        if args.single_kernel is not None:
+            del space["single_kernel"]
+        tuning = autotune.tune_single(scenes[0], space=space, start_kernel=args.single_kernel)
         tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"]),
                   "trial_ms": [[{k: t[k] for k in space}, round(t["ms"], 4)] for t in tuning["trials"]]}
 
@@ -560,8 +568,11 @@ def main():
 
     if rank != 0:
         return
-    kern = ("plain_kernel" if args.path == "plain" else
-            "batch_plain_kernel" if F.fr_get_tuning().batch_kernel == 1 else "persist_kernel")
+    tu = F.fr_get_tuning()
+    if args.path == "plain":  # the kernel fr_render_* launches under the tuned single_kernel
+        kern = {0: "plain_kernel", 1: "persist_kernel", 2: "batch_plain_kernel"}[tu.single_kernel]
+    else:
+        kern = "batch_plain_kernel" if tu.batch_kernel == 1 else "persist_kernel"
     res = {
         "metric": "Mrays/s", "value": value, "unit": "Mrays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -576,7 +587,7 @@ def main():
         "per_step": {"rays": rays_per_step, "primary_rays": counts[0], "shadow_rays": counts[1],
                      "mirror_rays": counts[6], "de_calls": de_per_step, "orbit_iters": iters_per_step},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, args.path)),
+                     "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, kern)),
                      "kernel": kern,
                      "flops_per_step": flops_per_step,
                      "peak_basis": "FP32 FFMA: %d SMs x %d lanes x 2 flops x %.0f MHz (max clock)" % (

@@ -203,7 +203,10 @@ typedef struct {
     int32_t refill_threshold;    /* refill a warp once this many lanes are idle (1..32) */
     int32_t persist_unroll;      /* Julia orbit steps per scheduling round: 1, 2, 4, 8  */
     int32_t single_kernel;       /* fr_render_julia/mandelbulb: 0 nested loops per thread,
-                                    1 lane state machine (one DE call site), no queue  */
+                                    1 lane state machine (one DE call site), no queue,
+                                    2 the batch kernel (batch_kernel 1's code, which
+                                    the compiler allocates differently) with the one
+                                    request.  Same images bit for bit.               */
     int32_t batch_kernel;        /* fr_render_batch: 0 persistent kernel with the pixel
                                     queue, 1 (default) one-ray-per-thread kernel over
                                     every tile of every request in one launch

@@ -8,6 +8,7 @@ For fr_render_batch (tune):
   refill_threshold   idle lanes that trigger a warp refill (the compaction interval)
   persist_unroll     Julia orbit steps per scheduling round (the unroll depth)
 For one request through fr_render_julia / fr_render_mandelbulb (tune_single):
+  single_kernel      0 the single-request kernel, 2 the batch kernel's code
   plain_block, plain_unroll (orbit-loop unroll depth) and tile_order.
 The search is coordinate descent from the current setting: each knob in turn is
 swept with the others fixed, each candidate timed with CUDA events (median of a
@@ -37,6 +38,7 @@ SPACE = {
     "persist_unroll": (2, 4, 8),
 }
 SINGLE_SPACE = {
+    "single_kernel": (0, 2),
     "plain_block": (64, 128, 256),
     "plain_unroll": (1, 2, 4),
     "tile_order": (0, 1, 2),
@@ -111,11 +113,13 @@ def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=
 
 
 def tune_single(scene, reps: int = 9, passes: int = 1, space: dict | None = None, log=None,
-                margin: float = 0.01) -> dict:
-    """The same search for one request through the single-request kernel (the
-    nested-loop kernel, single_kernel 0, is the one tuned)."""
+                margin: float = 0.01, start_kernel: int | None = None) -> dict:
+    """The same search for one request through fr_render_julia /
+    fr_render_mandelbulb, starting from the single-request kernel
+    (single_kernel 0, or start_kernel); the lane state machine (1) is not a
+    candidate."""
     out = api.alloc_image(scene)
-    apply({"single_kernel": 0})
+    apply({"single_kernel": 0 if start_kernel is None else start_kernel})
     return _descent(lambda: _time_single(scene, out, reps), space or SINGLE_SPACE, lambda k, c: True, passes,
                     log, margin)
 

@@ -258,7 +258,7 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
         return fail(FR_EINVAL, "persist_ctas_per_sm outside 0..32");
     if (t->refill_threshold < 1 || t->refill_threshold > 32)
         return fail(FR_EINVAL, "refill_threshold outside 1..32");
-    if (t->single_kernel != 0 && t->single_kernel != 1) return fail(FR_EINVAL, "single_kernel must be 0 or 1");
+    if (t->single_kernel < 0 || t->single_kernel > 2) return fail(FR_EINVAL, "single_kernel must be 0, 1 or 2");
     if (t->batch_kernel != 0 && t->batch_kernel != 1) return fail(FR_EINVAL, "batch_kernel must be 0 or 1");
     if (t->tile_order < 0 || t->tile_order > 2) return fail(FR_EINVAL, "tile_order must be 0, 1 or 2");
     std::lock_guard<std::mutex> lk(g_tuning_mu);
@@ -280,6 +280,21 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
         A.queue = nullptr;
         return launched(fr::launch_lanes(A, tu.plain_block, tu.persist_unroll, count, R.shading != 0,
                                          (cudaStream_t)stream));
+    }
+    if (tu.single_kernel == 2) {
+        // sides of at most 65535 make at most 1.4e8 tiles: the grid stays below the CTA limit
+        static thread_local fr::BatchArgs A;
+        const long long warps_per_cta = tu.plain_block / 32;
+        const long long ctas = (R.n_units / 32 + warps_per_cta - 1) / warps_per_cta;
+        A.reqs[0] = R;
+        A.reqs[0].unit_begin = 0;
+        A.reqs[0].tile_order = tu.tile_order;
+        A.n_reqs = 1;
+        A.total_units = ctas;
+        A.refill_threshold = 1;
+        A.queue = nullptr;
+        return launched(fr::launch_batch_plain(A, ctas, tu.plain_block, tu.plain_unroll, count, R.shading != 0,
+                                               (cudaStream_t)stream));
     }
     fr::DevReq Q = R;
     Q.tile_order = tu.tile_order;

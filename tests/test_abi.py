@@ -185,9 +185,13 @@ def test_tuning_roundtrip_and_checks(F):
         bad = F.fr_tuning(*old)
         bad.tile_order = v
         assert F.fr_set_tuning(bad) == F.FR_EINVAL and "tile_order" in F.fr_last_error()
+        bad = F.fr_tuning(*old)
+        bad.single_kernel = v
+        assert F.fr_set_tuning(bad) == F.FR_EINVAL and "single_kernel" in F.fr_last_error()
     good = F.fr_tuning(*old)
     good.plain_block = 64
     good.tile_order = 2
+    good.single_kernel = 2
     assert F.fr_set_tuning(good) == F.FR_OK
     assert F.fr_get_tuning().plain_block == 64 and F.fr_get_tuning().tile_order == 2
     assert F.fr_set_tuning(F.fr_tuning(*old)) == F.FR_OK

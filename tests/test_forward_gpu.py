@@ -102,7 +102,8 @@ def test_jittered_samples(api, orc):
 
 @pytest.mark.parametrize("block,unroll,single,order", [(32, 1, 0, 0), (64, 2, 0, 0), (256, 4, 0, 0), (128, 1, 0, 0),
                                                       (128, 1, 0, 1), (64, 2, 0, 2), (32, 4, 0, 1), (256, 1, 0, 2),
-                                                      (128, 1, 1, 0), (64, 2, 1, 0), (256, 8, 1, 0)])
+                                                      (128, 1, 1, 0), (64, 2, 1, 0), (256, 8, 1, 0),
+                                                      (128, 1, 2, 0), (64, 2, 2, 1), (256, 1, 2, 2)])
 def test_launch_shapes_give_identical_images(api, block, unroll, single, order):
     from paper_2102_01747_gb300 import _ffi as F
 
@@ -113,7 +114,7 @@ def test_launch_shapes_give_identical_images(api, block, unroll, single, order):
     ref = (gpu(api, s), gpu(api, j))
     t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
     t.plain_block, t.single_kernel, t.tile_order = block, single, order
-    if single:
+    if single == 1:
         t.persist_unroll = unroll  # the lane state machine's Julia steps per round
     else:
         t.plain_unroll = unroll
