@@ -106,3 +106,28 @@ def test_tile_orders_bitwise_at_full_size(api, name):
         F.fr_set_tuning(old)
     for o in imgs[1:]:
         assert torch.equal(o["rgba8"], imgs[0]["rgba8"]) and torch.equal(o["depth"], imgs[0]["depth"])
+
+
+@pytest.mark.parametrize("name", ["bulb_1080p", "stress_bulb_4k"])
+def test_single_request_kernels_bitwise_at_full_size(api, name):
+    """fr_render_mandelbulb on the batch kernel (single_kernel 2, what the
+    autotuner keeps for these frames) gives the single-request kernel's image
+    bit for bit at full size."""
+    import torch
+
+    from paper_2102_01747_gb300 import _ffi as F
+
+    s = W.bulb_1080p(10) if name == "bulb_1080p" else W.stress_bulb_4k(60)
+    old = F.fr_get_tuning()
+    imgs = []
+    try:
+        for sk in (0, 2):
+            t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
+            t.single_kernel = sk
+            assert F.fr_set_tuning(t) == F.FR_OK
+            out = api.render(s, rgba8=True, depth=True)
+            torch.cuda.synchronize()
+            imgs.append(out)
+    finally:
+        F.fr_set_tuning(old)
+    assert torch.equal(imgs[0]["rgba8"], imgs[1]["rgba8"]) and torch.equal(imgs[0]["depth"], imgs[1]["depth"])
