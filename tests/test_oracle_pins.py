@@ -615,19 +615,24 @@ def test_bulb_trap_on_polar_axis(orc):
 
 
 # ------------------------------------------------------ analytic normal (Sec. 2)
-def test_analytic_normal_reduces_to_complex_derivative(orc):
+@pytest.mark.parametrize("p", [2, 3])
+def test_analytic_normal_reduces_to_complex_derivative(orc, p):
     """On span{1, i} with c there too, grad log|z_N| is conj(dz_N/dz_0) z_N in the
-    (x, y) plane (the chain rule D <- 2 z D in complex arithmetic) and 0 along z."""
+    (x, y) plane (the chain rule D <- p z^(p-1) D in complex arithmetic) and 0
+    along z; degree 3 with the listing's escape |z|^2 > 256."""
     rng = np.random.default_rng(41)
     s = W.julia_256(8, 8)
     s["normal_mode"] = "analytic"
-    c = complex(-0.2, 0.6)
+    s["p"] = p
+    if p == 3:
+        s["escape_r2"] = 256.0
+    c = complex(-0.2, 0.6) if p == 2 else complex(0.1, 0.55)
     s["c"] = (c.real, c.imag, 0.0, 0.0)
     for x, y in rng.uniform(-1.2, 1.2, (300, 2)):
         z, D = complex(x, y), 1.0 + 0j
         for _ in range(s["max_iter"]):
-            D = 2 * z * D
-            z = z * z + c
+            D = p * z ** (p - 1) * D
+            z = z ** p + c
             if abs(z) ** 2 > s["escape_r2"]:
                 break
         g = D.conjugate() * z
