@@ -13,9 +13,14 @@
  *   - sphere tracing from t = eps in steps of min(d, max_step) inside the
  *     interval left by a bounding sphere and the cutting plane     Listing "Julia Set ray cast", Sec. 3.1
  *   - normal = normalised gradient of d, tetrahedral (Eq. 5, Listing "Normal
- *     calculation") or central differences
+ *     calculation") or central differences, or grad G / |grad G| from the
+ *     orbit's Jacobian (Sec. 2)
  *   - closest-hit shading: Lambert with one directional light and an optional
- *     shadow ray (stands in for the Phong closest-hit of Listing "Closest-hit shader")
+ *     shadow ray, or the Phong + Fresnel-weighted mirror ray of Listing
+ *     "Closest-hit shader"; the listings' orbit-trap colour parameters as an
+ *     optional output
+ *   - the adjoint of the Julia render by implicit differentiation at the hit
+ *     (Sec. 2's level-set relations)
  *
  * Conventions shared by every entry point:
  *   - Device memory belongs to the caller.  Every pointer in fr_image, the
