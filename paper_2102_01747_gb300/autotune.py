@@ -31,7 +31,7 @@ from . import api
 
 SPACE = {
     "batch_kernel": (1, 0),
-    "plain_block": (64, 128, 256),
+    "plain_block": (32, 64, 128, 256),
     "tile_order": (0, 1, 2),
     "persist_block": (64, 128, 256),
     "refill_threshold": (1, 2, 4, 8, 16),
@@ -39,7 +39,7 @@ SPACE = {
 }
 SINGLE_SPACE = {
     "single_kernel": (0, 2),
-    "plain_block": (64, 128, 256),
+    "plain_block": (32, 64, 128, 256),
     "plain_unroll": (1, 2, 4),
     "tile_order": (0, 1, 2),
 }
