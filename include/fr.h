@@ -240,7 +240,8 @@ FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_pla
 FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs);
 
 /* Render n_reqs requests (mixed kinds and sizes) with one kernel launch per 64
- * requests (largest first).  Two schedules, picked by fr_tuning.batch_kernel:
+ * requests (costliest first: pixels x samples x iteration cap, weighted by
+ * fractal and shadows).  Two schedules, picked by fr_tuning.batch_kernel:
  *   1 (default)  one-ray-per-thread kernel over every tile of every request:
  *                each CTA belongs to one request and the hardware block
  *                scheduler hands CTAs to SMs as they free up, so the slow

