@@ -75,6 +75,9 @@ static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 // 64-request mixed batch, this build (64 registers as the compiler allocates
 // them) takes 33.0 ms and the one without it 35.0 ms, whether left at its 80
 // registers or capped at 64 (62); on 64 small requests 2.73 against 3.10 ms.
+// The same build renders single Lambert Mandelbulb frames faster than
+// plain_kernel (1080p: 1.03 against 1.06 ms), so fr_render_* can launch it
+// with the one request (fr_tuning.single_kernel = 2, autotuned).
 template <int U, bool COUNT, bool PHONG>
 __global__ void __launch_bounds__(256) batch_plain_kernel(const __grid_constant__ BatchArgs A)
 {
