@@ -33,16 +33,16 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # everything included (orbit step, DE epilogue, march update, stencils, camera
 # ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
 # divided by the iterations counted on the same scene (Mandelbulb n = 8 at
-# 1920x1080: 8.687 G / 50.88 M = 170.8, profiles/plain_kernel_mandelbulb_1080p.md;
+# 1920x1080: 8.534 G / 50.88 M = 167.7, profiles/plain_kernel_mandelbulb_1080p.md;
 # Julia p = 2 at 256x256: 364.9 M / 10.27 M = 35.6).  The degree-3 Julia figure
 # is the degree-2 one scaled by the ratio of their orbit-step arithmetic
 # (28 / 24); other Mandelbulb powers take the n = 8 figure (same calls per step).
-FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5, ("bulb", 8): 170.8}
+FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5, ("bulb", 8): 167.7}
 # DRAM bytes of one launch of the dominant kernel (by the kernel the tuned
 # configuration launches), from the ncu capture of the same command
 # (dram__bytes_read.sum + dram__bytes_write.sum); the frame's 16.6 MB of
 # stores are still in the 129 MB L2 when the kernel ends.
-TRAFFIC = {("bulb_1080p", "plain_kernel"): 1707264 + 1661696, ("bulb_1080p", "batch_plain_kernel"): 82176 + 3328}
+TRAFFIC = {("bulb_1080p", "plain_kernel"): 1390080 + 29952, ("bulb_1080p", "batch_plain_kernel"): 70400 + 1024}
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32)
 
 

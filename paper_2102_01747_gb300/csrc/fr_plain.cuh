@@ -71,15 +71,13 @@ static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 // CTAs to SMs as they free up, so the requests' slow pixels overlap instead of
 // each launch waiting for its own.  tile_begin of request r (in CTAs) is kept
 // in reqs[r].unit_begin.
-// Always compiled with the Mandelbulb's analytic normal: measured on the
-// 64-request mixed batch, this build (64 registers as the compiler allocates
-// them) takes 33.0 ms and the one without it 35.0 ms, whether left at its 80
-// registers or capped at 64 (62); on 64 small requests 2.73 against 3.10 ms.
-// The same build renders single Lambert Mandelbulb frames faster than
-// plain_kernel (1080p: 1.03 against 1.06 ms), so fr_render_* can launch it
-// with the one request (fr_tuning.single_kernel = 2, autotuned).
+// Always compiled with the Mandelbulb's analytic normal, and held to 72
+// registers (at most 256 threads per block, as fr_set_tuning enforces): left
+// to itself the compiler takes 80, with which the 64-request mixed batch runs
+// 36.0 ms against 33.3 (64 registers: 33.5).  fr_render_* can also launch it
+// with one request (fr_tuning.single_kernel = 2, autotuned).
 template <int U, bool COUNT, bool PHONG>
-__global__ void __launch_bounds__(256) batch_plain_kernel(const __grid_constant__ BatchArgs A)
+__global__ void __maxnreg__(72) batch_plain_kernel(const __grid_constant__ BatchArgs A)
 {
     const int warps = blockDim.x >> 5;
     const long long cta = blockIdx.x;
