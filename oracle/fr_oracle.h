@@ -24,6 +24,16 @@
  *   tetrahedral gradient                                    Eq. 5 and Listing "Normal calculation"
  *   hit -> normal -> shade                                  Listings "JuliaDistance", "Closest-hit shader"
  *   Phong + Fresnel-Schlick reflection bounce               closest-hit listing of Sec. 3.1
+ *   analytic normal grad G / |grad G| (Julia, Mandelbulb)   Sec. 2
+ *   gradient of the Julia render (dual numbers)             Sec. 2, implicit differentiation
+ *
+ * Every part is pinned by tests/test_oracle_*.py against something other than
+ * itself (closed forms, complex-arithmetic orbits, brute force, finite
+ * differences, symmetries).  Parity unpinned: the DE's upper bracket in 3D
+ * (only the lower bound has a theorem), the colour at a mirror ray's hit (its
+ * structure is pinned, not its value), orbit-trap values of orbits that stay
+ * bounded, and whole images beyond their component pins (the paper prints no
+ * values).
  */
 #ifndef FR_ORACLE_H
 #define FR_ORACLE_H
