@@ -136,6 +136,10 @@ def fp32_peak_tflops(clock_mhz: float, sms: int) -> float:
     return sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
 
 
+def _stride_words(stride):
+    return "every pixel" if stride == 1 else "every %d-th pixel" % stride
+
+
 def _oracle_sample(scenes, stride):
     """Pixel sample of the step's scenes: every stride-th pixel of each."""
     import numpy as np
@@ -172,7 +176,7 @@ def run_reference(args, scenes, desc, rank, world):
         rays += _oracle_rays(oracle, scenes, samples, threads)
     dt = time.perf_counter() - t0
     value = rays / dt / 1e6
-    sample = "every %d-th pixel of each image (%d pixels per step)" % (stride, sum(map(len, samples)))
+    sample = "%s of each image (%d pixels per step)" % (_stride_words(stride), sum(map(len, samples)))
     print(json.dumps({
         "impl": "reference", "metric": "Mrays/s", "value": value, "unit": "Mrays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -208,7 +212,7 @@ def cpu_baseline(scenes, budget_s: float = 12.0):
         dt += time.perf_counter() - t1
         reps += 1
     return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": "every %d-th pixel of each image, %d pass(es), %.1f s" % (stride, reps, dt)}
+            "sample": "%s of each image, %d pass%s, %.1f s" % (_stride_words(stride), reps, "" if reps == 1 else "es", dt)}
 
 
 class Renderer:
