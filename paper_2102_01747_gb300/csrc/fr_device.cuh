@@ -3,8 +3,9 @@
 // One request is a DevReq: the public parameter structs of include/fr.h resolved
 // on the host into what the kernels read (camera basis, normalised light,
 // squared radii, output pointers).  Every routine here computes in FP32 with
-// the accurate CUDA math library (no --use_fast_math, no __xxxf intrinsics);
-// the compiler may contract a*b+c into FFMA.
+// the accurate CUDA math library (no --use_fast_math, no approximate __xxxf
+// intrinsics) and spells out every rounding step (mul/add/sub/dvd, fmaf), so
+// that all kernels compute the same bits for the same ray.
 //
 // Paper passages (da Silva, Novello, Lopes, Velho, "Real-time rendering of
 // complex fractals"):
@@ -14,9 +15,12 @@
 //              sphere and the cutting plane (Fig. 1)
 //   march      Listing "Julia Set ray cast" (step min(d, max_step), hit d < eps,
 //              miss t > t1, step cap counts as a hit)
-//   normal     Eq. 5 / Listing "Normal calculation" (tetrahedral), or central
-//              differences
-//   shade      Lambert closest-hit with an optional shadow ray
+//   normal     Eq. 5 / Listing "Normal calculation" (tetrahedral), central
+//              differences, or grad G / |grad G| from the orbit's Jacobian
+//              (Sec. 2; julia_analytic_normal, bulb_analytic_normal)
+//   shade      Lambert closest-hit with an optional shadow ray, or Phong with
+//              a Fresnel-weighted mirror ray (Listing "Closest-hit shader")
+//   orbit_trap the listings' colour parameters
 #pragma once
 
 #include <cstdint>
