@@ -133,8 +133,9 @@ def lib():
         L.orc_normal_field_d.argtypes = [i, pd, pd, i, d, pd, pd]
         L.orc_shade_d.argtypes = [P(OrcScene), pd, d, pd]
         L.orc_shade_phong_d.argtypes = [P(OrcScene), pd, pd, d, pd, pd]
-        L.orc_julia_grad_d.argtypes = [P(OrcScene), pd, pd, ctypes.c_void_p, pd, i]
-        L.orc_julia_grad_d.restype = i
+        for fn in (L.orc_julia_grad_d, L.orc_bulb_grad_d):
+            fn.argtypes = [P(OrcScene), pd, pd, ctypes.c_void_p, pd, i]
+            fn.restype = i
         _lib = L
     return _lib
 
@@ -376,14 +377,16 @@ def quantize(x, precision: str = "f64") -> int:
 def julia_grad(scene: dict, d_rgba, d_depth=None, mask=None, threads: int = 1) -> np.ndarray:
     """Reference vector-Jacobian product of the Julia render (double, forward-mode
     dual numbers, implicit differentiation at the hit).  Returns the 11-vector
-    (dc[4], dplane_n[3], dplane_o, dlight_dir[3])."""
+    (dc[4], dplane_n[3], dplane_o, dlight_dir[3]).  A Mandelbulb scene gives
+    the same vector with dc = 0 (the fractal has no parameter c)."""
     s = scene_struct(scene)
     W, H = s.width, s.height
     dr = _arr(d_rgba).reshape(W * H * 4)
     dd = None if d_depth is None else _arr(d_depth).reshape(W * H)
     mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(W * H))
     g = np.zeros(11)
-    rc = lib().orc_julia_grad_d(ctypes.byref(s), _ptr(dr), None if dd is None else _ptr(dd),
+    fn = lib().orc_julia_grad_d if scene["kind"] == "julia" else lib().orc_bulb_grad_d
+    rc = fn(ctypes.byref(s), _ptr(dr), None if dd is None else _ptr(dd),
                                 None if mk is None else mk.ctypes.data, _ptr(g), int(threads))
     if rc != 0:
         raise ValueError("oracle gradient rejected the scene")

@@ -172,6 +172,12 @@ uint32_t orc_quantize_f(float x);
 int orc_julia_grad_d(const orc_scene *s, const double *d_rgba, const double *d_depth,
                      const uint8_t *mask, double grad[11], int n_threads);
 
+/* The same for a Mandelbulb render: the fractal has no parameter c
+ * (grad[0..3] = 0), so surface hits move only through Lambert's n.L (light
+ * direction) and cut-face hits through the plane and the light. */
+int orc_bulb_grad_d(const orc_scene *s, const double *d_rgba, const double *d_depth,
+                    const uint8_t *mask, double grad[11], int n_threads);
+
 #ifdef __cplusplus
 }
 #endif
