@@ -319,6 +319,22 @@ FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plan
  * FR_ENOMEM (ws_bytes too small), FR_ECUDA.  The workspace is checked before
  * anything else. */
 FR_API size_t fr_backward_workspace_bytes(void);
+
+/* Vector-Jacobian product of a Mandelbulb render (spp = 1, Lambert), same
+ * cotangents and 11-float layout as fr_render_backward.  The fractal has no
+ * parameter c (grad[0..3] gets nothing); a surface hit moves with neither the
+ * cut plane nor the light, so it adds only Lambert's d(n.L)/d(light dir) with
+ * n the forward pass's normal at the saved hit, and a cut-face hit adds the
+ * plane's and the light's terms as in fr_render_backward.
+ *   workspace  NULL (the library's accumulator: calls must not overlap) or
+ *              fr_backward_workspace_bytes() bytes of device memory, 16-byte
+ *              aligned, as for fr_render_backward_ws
+ * Errors: FR_EINVAL (spp != 1, Phong shading, NULL buffers, bad parameters,
+ * misaligned workspace), FR_ENOMEM (ws_bytes too small), FR_ECUDA. */
+FR_API fr_status fr_render_backward_mandelbulb(const fr_bulb_params *params, const fr_plane *plane,
+                                               const fr_camera *camera, const fr_light *light,
+                                               const float *saved, const float *d_rgba, const float *d_depth,
+                                               float *grad, void *workspace, size_t ws_bytes, void *stream);
 FR_API fr_status fr_render_backward_ws(const fr_julia_params *params, const fr_plane *plane,
                                        const fr_camera *camera, const fr_light *light,
                                        const float *saved, const float *d_rgba, const float *d_depth,

@@ -88,6 +88,10 @@ SIGNATURES = {
                                      ctypes.POINTER(fr_camera), ctypes.POINTER(fr_light), c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p]),
     "fr_backward_workspace_bytes": (ctypes.c_size_t, []),
+    "fr_render_backward_mandelbulb": (c_int32, [ctypes.POINTER(fr_bulb_params), ctypes.POINTER(fr_plane),
+                                                ctypes.POINTER(fr_camera), ctypes.POINTER(fr_light), c_void_p,
+                                                c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
+                                                c_void_p]),
     "fr_render_backward_ws": (c_int32, [ctypes.POINTER(fr_julia_params), ctypes.POINTER(fr_plane),
                                         ctypes.POINTER(fr_camera), ctypes.POINTER(fr_light), c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
@@ -176,6 +180,13 @@ def fr_render_backward_ws(params, plane, camera, light, saved, d_rgba, d_depth, 
     return load().fr_render_backward_ws(ctypes.byref(params), ctypes.byref(plane) if plane else None,
                                         ctypes.byref(camera), ctypes.byref(light), saved, d_rgba,
                                         d_depth, grad, workspace, int(ws_bytes), stream)
+
+
+def fr_render_backward_mandelbulb(params, plane, camera, light, saved, d_rgba, d_depth, grad, workspace=None,
+                                  ws_bytes=0, stream=None):
+    return load().fr_render_backward_mandelbulb(ctypes.byref(params), ctypes.byref(plane) if plane else None,
+                                                ctypes.byref(camera), ctypes.byref(light), saved, d_rgba,
+                                                d_depth, grad, workspace, int(ws_bytes), stream)
 
 
 def fr_get_tuning():

@@ -79,6 +79,14 @@ def backward_raw(scene, saved, d_rgba, d_depth=None, grad=None, workspace=None):
     (accumulated into grad)."""
     if grad is None:
         grad = torch.zeros(11, dtype=torch.float32, device=saved.device)
+    if scene["kind"] == "bulb":  # plane and light only (the Mandelbulb has no c)
+        st = F.fr_render_backward_mandelbulb(
+            api.bulb_params(scene), api.plane_struct(scene), api.camera_struct(scene), api.light_struct(scene),
+            saved.data_ptr(), d_rgba.data_ptr(), None if d_depth is None else d_depth.data_ptr(), grad.data_ptr(),
+            None if workspace is None else workspace.data_ptr(),
+            0 if workspace is None else workspace.numel() * workspace.element_size(), api.current_stream(saved.device))
+        F.check(st)
+        return grad
     args = (api.julia_params(scene), api.plane_struct(scene), api.camera_struct(scene),
             api.light_struct(scene), saved.data_ptr(), d_rgba.data_ptr(),
             None if d_depth is None else d_depth.data_ptr(), grad.data_ptr())

@@ -426,6 +426,10 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
     return FR_OK;
 }
 
+static fr_status resolve_backward_common(fr::BwdArgs &A, const fr_plane *plane, const fr_camera *camera,
+                                         const fr_light *light, const float *saved, const float *d_rgba,
+                                         const float *d_depth, float *grad);
+
 // checks and resolves the arguments of a backward call into A (acc/done left NULL)
 static fr_status resolve_backward(fr::BwdArgs &A, const fr_julia_params *params, const fr_plane *plane,
                                   const fr_camera *camera, const fr_light *light, const float *saved,
@@ -434,11 +438,19 @@ static fr_status resolve_backward(fr::BwdArgs &A, const fr_julia_params *params,
     std::memset(&A, 0, sizeof A);
     fr_status st = resolve_julia(A.R, params);
     if (st != FR_OK) return st;
-    if (light && light->shading != FR_SHADE_LAMBERT)
-        return fail(FR_EINVAL, "backward supports Lambert shading");
     if (params->max_iter > fr::kMaxBwdIter)
         return fail(FR_EINVAL, "backward keeps at most %d orbit iterations (max_iter %d)", fr::kMaxBwdIter,
                     params->max_iter);
+    return resolve_backward_common(A, plane, camera, light, saved, d_rgba, d_depth, grad);
+}
+
+static fr_status resolve_backward_common(fr::BwdArgs &A, const fr_plane *plane, const fr_camera *camera,
+                                         const fr_light *light, const float *saved, const float *d_rgba,
+                                         const float *d_depth, float *grad)
+{
+    fr_status st;
+    if (light && light->shading != FR_SHADE_LAMBERT)
+        return fail(FR_EINVAL, "backward supports Lambert shading");
     if (!camera) return fail(FR_EINVAL, "camera is NULL");
     if (camera->spp != 1) return fail(FR_EINVAL, "backward needs spp == 1 (got %d)", camera->spp);
     if (!saved || !d_rgba || !grad) return fail(FR_EINVAL, "saved, d_rgba and grad must be given");
@@ -464,6 +476,33 @@ FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plan
     fr::BwdArgs A;
     const fr_status st = resolve_backward(A, params, plane, camera, light, saved, d_rgba, d_depth, grad);
     if (st != FR_OK) return st;
+    return launched(fr::launch_backward(A, (cudaStream_t)stream));
+}
+
+FR_API fr_status fr_render_backward_mandelbulb(const fr_bulb_params *params, const fr_plane *plane,
+                                               const fr_camera *camera, const fr_light *light,
+                                               const float *saved, const float *d_rgba, const float *d_depth,
+                                               float *grad, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (workspace && !aligned(workspace, 16)) return fail(FR_EINVAL, "workspace must be 16-byte aligned");
+    if (workspace && ws_bytes < fr_backward_workspace_bytes())
+        return fail(FR_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, fr_backward_workspace_bytes());
+    fr::BwdArgs A;
+    std::memset(&A, 0, sizeof A);
+    fr_status st = resolve_bulb(A.R, params);
+    if (st != FR_OK) return st;
+    if ((st = resolve_backward_common(A, plane, camera, light, saved, d_rgba, d_depth, grad)) != FR_OK)
+        return st;
+    if (workspace) {
+        A.acc = static_cast<double *>(workspace);
+        A.done = reinterpret_cast<unsigned int *>(static_cast<char *>(workspace) + 11 * sizeof(double));
+        const cudaError_t e =
+            cudaMemsetAsync(workspace, 0, fr_backward_workspace_bytes(), (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return launched(e);
+        }
+    }
     return launched(fr::launch_backward(A, (cudaStream_t)stream));
 }
 

@@ -171,6 +171,56 @@ __device__ __forceinline__ float3 tap_weight(int mode, float h, int k)
     return v3(j == 0 ? s : 0.0f, j == 1 ? s : 0.0f, j == 2 ? s : 0.0f);
 }
 
+// Cut-face hit: t = (o - n.ro) / (n.rd), normal n/|n|; Lambert through n and L
+__device__ __forceinline__ void face_grad(const BwdArgs &A, float3 x, float3 rd, float3 L, float W, float vis,
+                                          float gd, float gsum[11])
+{
+    const DevReq &R = A.R;
+    const float3 nh = v3(R.plane_hat);
+    const float3 nraw = v3(R.plane);
+    const float ndl = dot3(nh, L);
+    const float act = ndl > 0.0f ? W * R.kd * vis : 0.0f;
+    const float nrd = dot3(nraw, rd);
+    gsum[4] += act * (L.x - nh.x * ndl) / A.plane_norm - gd * x.x / nrd;
+    gsum[5] += act * (L.y - nh.y * ndl) / A.plane_norm - gd * x.y / nrd;
+    gsum[6] += act * (L.z - nh.z * ndl) / A.plane_norm - gd * x.z / nrd;
+    gsum[7] += gd / nrd;
+    gsum[8] += act * (nh.x - L.x * ndl) / A.light_norm;
+    gsum[9] += act * (nh.y - L.y * ndl) / A.light_norm;
+    gsum[10] += act * (nh.z - L.z * ndl) / A.light_norm;
+}
+
+// The Mandelbulb has no parameter c and its surface hits move with neither
+// the plane nor the light: only Lambert's n.L moves, through the light
+// direction, with n the forward pass's normal at the saved hit.
+__device__ void pixel_grad_bulb(const BwdArgs &A, int px, int py, float gsum[11])
+{
+    const DevReq &R = A.R;
+    const long long idx = (long long)py * R.width + px;
+    const float4 sv = A.saved[idx];
+    const uint32_t flags = __float_as_uint(sv.w);
+    if (!(flags & kFlagHit)) return;
+    const float4 dr = A.d_rgba[idx];
+    const float W = dr.x * R.albedo.x + dr.y * R.albedo.y + dr.z * R.albedo.z;
+    const float gd = A.d_depth ? A.d_depth[idx] : 0.0f;
+    const float vis = (flags & kFlagShadow) ? 0.0f : 1.0f;
+    float3 ro, rd;
+    camera_ray(R, px, py, 0, ro, rd);
+    const float3 x = v3(sv.x, sv.y, sv.z);
+    const float3 L = v3(R.light);
+    if (flags & kFlagFace) {
+        face_grad(A, x, rd, L, W, vis, gd, gsum);
+        return;
+    }
+    Counters cnt;
+    const float3 n = normal_at<1, 1, false, true>(R, x, rd, cnt);
+    const float ndl = dot3(n, L);
+    const float act = ndl > 0.0f ? W * R.kd * vis : 0.0f;
+    gsum[8] += act * (n.x - L.x * ndl) / A.light_norm;
+    gsum[9] += act * (n.y - L.y * ndl) / A.light_norm;
+    gsum[10] += act * (n.z - L.z * ndl) / A.light_norm;
+}
+
 template <int P>
 __device__ void pixel_grad(const BwdArgs &A, int px, int py, float gsum[11])
 {
@@ -189,18 +239,7 @@ __device__ void pixel_grad(const BwdArgs &A, int px, int py, float gsum[11])
     const float3 L = v3(R.light);
 
     if (flags & kFlagFace) {
-        const float3 nh = v3(R.plane_hat);
-        const float3 nraw = v3(R.plane);
-        const float ndl = dot3(nh, L);
-        const float act = ndl > 0.0f ? W * R.kd * vis : 0.0f;
-        const float nrd = dot3(nraw, rd);
-        gsum[4] += act * (L.x - nh.x * ndl) / A.plane_norm - gd * x.x / nrd;
-        gsum[5] += act * (L.y - nh.y * ndl) / A.plane_norm - gd * x.y / nrd;
-        gsum[6] += act * (L.z - nh.z * ndl) / A.plane_norm - gd * x.z / nrd;
-        gsum[7] += gd / nrd;
-        gsum[8] += act * (nh.x - L.x * ndl) / A.light_norm;
-        gsum[9] += act * (nh.y - L.y * ndl) / A.light_norm;
-        gsum[10] += act * (nh.z - L.z * ndl) / A.light_norm;
+        face_grad(A, x, rd, L, W, vis, gd, gsum);
         return;
     }
 
@@ -284,7 +323,12 @@ __global__ void __launch_bounds__(256) backward_kernel(const __grid_constant__ B
     float gsum[11];
 #pragma unroll
     for (int k = 0; k < 11; k++) gsum[k] = 0.0f;
-    if (px < R.width && py < R.height) pixel_grad<P>(A, px, py, gsum);
+    if (px < R.width && py < R.height) {
+        if constexpr (P == 0)
+            pixel_grad_bulb(A, px, py, gsum);
+        else
+            pixel_grad<P>(A, px, py, gsum);
+    }
 
     __shared__ float part[8][11];
     const int warp = threadIdx.x >> 5;
@@ -333,7 +377,9 @@ cudaError_t launch_backward(const BwdArgs &A, cudaStream_t s)
     const long long tiles_y = (A.R.height + kTileH - 1) / kTileH;
     const long long threads = (long long)A.R.tiles_x * tiles_y * 32;
     const long long grid = (threads + block - 1) / block;
-    if (A.R.power == 2)
+    if (A.R.kind == 1)  // Mandelbulb (P = 0)
+        backward_kernel<0><<<(unsigned)grid, block, 0, s>>>(A);
+    else if (A.R.power == 2)
         backward_kernel<2><<<(unsigned)grid, block, 0, s>>>(A);
     else
         backward_kernel<3><<<(unsigned)grid, block, 0, s>>>(A);

@@ -296,6 +296,22 @@ def test_backward_workspace_checked_first(F):
     assert st == F.FR_EINVAL and "must be given" in F.fr_last_error(), F.fr_last_error()
 
 
+def test_mandelbulb_backward_host_checks(F):
+    """fr_render_backward_mandelbulb refuses on the host; no pointer below is
+    ever dereferenced."""
+    s = W.bulb_1080p(0, 16, 16)
+    p, pl, cam, li = _structs(s)
+    st = F.fr_render_backward_mandelbulb(p, pl, cam, li, None, None, None, None)
+    assert st == F.FR_EINVAL and "must be given" in F.fr_last_error(), F.fr_last_error()
+    st = F.fr_render_backward_mandelbulb(p, pl, cam, li, None, None, None, None, 8, 128)
+    assert st == F.FR_EINVAL and "aligned" in F.fr_last_error()
+    st = F.fr_render_backward_mandelbulb(p, pl, cam, li, None, None, None, None, 256, 64)
+    assert st == F.FR_ENOMEM
+    ph = _structs(W.phong(s))
+    st = F.fr_render_backward_mandelbulb(*ph, None, None, None, None)
+    assert st == F.FR_EINVAL and "Lambert" in F.fr_last_error()
+
+
 def test_c_client_compiles_against_the_header():
     """A plain C99 program (tests/c_client/render_request.c) compiles with
     -Wall -Wextra -Werror against include/fr.h and links against libfr.so."""
