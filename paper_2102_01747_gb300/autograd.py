@@ -11,6 +11,11 @@ are 1-D tensors: c (4), plane_n (3), plane_o (1), light_dir (3).  Every other
 parameter is taken from `scene`.  Gradients with respect to the alpha channel
 are ignored (alpha is piecewise constant); so are depth cotangents on pixels
 that miss.
+
+    rgba, depth = bulb_render(scene, plane_n, plane_o, light_dir)
+
+is the same for a Mandelbulb scene, differentiable with respect to the cut
+plane and the light (fr_render_backward_mandelbulb; the fractal has no c).
 """
 from __future__ import annotations
 
@@ -66,6 +71,40 @@ class JuliaRender(torch.autograd.Function):
 
 def julia_render(scene, c, plane_n, plane_o, light_dir):
     return JuliaRender.apply(c, plane_n, plane_o, light_dir, scene)
+
+
+class BulbRender(torch.autograd.Function):
+    """The Mandelbulb render, differentiable with respect to the cut plane and
+    the light (fr_render_backward_mandelbulb; the fractal has no parameter c)."""
+
+    @staticmethod
+    def forward(ctx, plane_n, plane_o, light_dir, scene):
+        s = copy.deepcopy(scene)
+        s["plane"] = {"n": tuple(float(v) for v in plane_n.detach().cpu().tolist()),
+                      "o": float(plane_o.detach().cpu().reshape(-1)[0])}
+        s["light"]["dir"] = tuple(float(v) for v in light_dir.detach().cpu().tolist())
+        if s["kind"] != "bulb" or s["camera"]["spp"] != 1:
+            raise ValueError("the differentiable Mandelbulb render takes a Mandelbulb scene with spp = 1")
+        out = api.render(s, rgba8=False, rgba=True, depth=True, saved=True)
+        ctx.scene = s
+        ctx.save_for_backward(out["saved"])
+        ctx.in_dev = (plane_n.device, plane_o.device, light_dir.device)
+        return out["rgba"], out["depth"]
+
+    @staticmethod
+    def backward(ctx, d_rgba, d_depth):
+        (saved,) = ctx.saved_tensors
+        d_rgba = (torch.zeros_like(saved) if d_rgba is None else d_rgba).float().contiguous()
+        dd = None
+        if d_depth is not None:
+            dd = torch.nan_to_num(d_depth.float(), nan=0.0, posinf=0.0, neginf=0.0).contiguous()
+        grad = backward_raw(ctx.scene, saved, d_rgba, dd, workspace=backward_workspace(saved.device))
+        dn, do, dl = ctx.in_dev
+        return grad[4:7].to(dn), grad[7:8].to(do), grad[8:11].to(dl), None
+
+
+def bulb_render(scene, plane_n, plane_o, light_dir):
+    return BulbRender.apply(plane_n, plane_o, light_dir, scene)
 
 
 def backward_workspace(device) -> torch.Tensor:
