@@ -614,6 +614,103 @@ def test_bulb_trap_on_polar_axis(orc):
             assert t[1] == y0 and t[2] == 0.0 and abs(t[3] - y0 * y0) <= 1e-15
 
 
+def _axis_orbit(y0, n, trips):
+    """The orbit of Eq. 1 on the polar axis: y <- y^n + y0 from y = y0."""
+    y = y0
+    for _ in range(trips):
+        y = y**n + y0
+    return y
+
+
+def test_bulb_trap_takes_the_previous_m(orc):
+    """The listing folds the new w into the running minimum beside the m of the
+    step before, so 'min m' leaves out the final iterate's |w|^2 while 'min |w.y|'
+    includes it.  On the -y axis, orbits of y <- y^n + y0 shrink and grow again;
+    wherever the last iterate is the smallest, the two orders of the update give
+    different minima, and the oracle must give the listing's."""
+    s = W.bulb_1080p(0, 8, 8)
+    checked = 0
+    for n in (2, 3, 8):
+        for y0 in np.linspace(-1.2, -0.05, 24):
+            for trips in range(1, 13):
+                ys = [float(y0)]
+                for _ in range(trips):
+                    ys.append(ys[-1] ** n + float(y0))
+                    if abs(ys[-1]) > s["bailout"]:
+                        break
+                if abs(ys[-1]) > s["bailout"]:
+                    continue  # escaped: then the final m is the largest and the orders agree
+                m = [y * y for y in ys]
+                old_m, new_m = min(m[:-1]), min(m)
+                if abs(old_m - new_m) <= 1e-3 * new_m:
+                    continue
+                s.update(n=n, max_iter=trips)
+                t = orc.trap(s, [0.0, y0, 0.0])
+                assert abs(t[3] - old_m) <= 1e-12 * old_m, (n, y0, trips, t, old_m, new_m)
+                assert abs(t[1] - min(abs(y) for y in ys)) <= 1e-12, (n, y0, trips, t)
+                assert abs(t[0] - m[-1]) <= 1e-12 * max(1.0, m[-1])
+                checked += 1
+    assert checked > 30
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 9])
+def test_bulb_de_derivative_on_polar_axis(orc, n):
+    """On the +y axis Eq. 1 is the real map y <- y^n + y0 (polar angle 0), every
+    iterate stays positive, and the listing's running derivative
+    dz <- n |w|^(n-1) dz + 1 from dz = 1 is exactly d y_N / d y0 (the '+1' because
+    c = y0 enters every step, |w| taken before the step).  So the DE must equal
+    0.25 log(m) sqrt(m) / (d y_N / d y0), the derivative of the real map over the
+    oracle's own trip count taken by the complex step (Squire and Trapp, 1998:
+    f'(x) = Im f(x + i h) / h up to h^2, with no cancellation), in Python's
+    complex arithmetic; dropping the '+1', or taking |w| after the step, changes
+    the DE by 10 % or more."""
+    s = W.bulb_1080p(0, 8, 8)
+    s["n"] = n
+    ys = np.concatenate([np.linspace(0.05, 0.6, 12), np.linspace(0.62, 1.6, 24)])
+    d, _, trips, m2 = orc.de(s, np.stack([0 * ys, ys, 0 * ys], 1))
+    for y0, dd, N, mm in zip(ys, d, trips, m2):
+        h = 1e-30
+        deriv = _axis_orbit(complex(float(y0), h), n, int(N)).imag / h
+        m = _axis_orbit(float(y0), n, int(N)) ** 2
+        assert abs(mm - m) <= 1e-12 * m
+        want = 0.25 * math.log(m) * math.sqrt(m) / deriv
+        assert abs(dd - want) <= 1e-9 * abs(want), (n, y0, N, dd, want)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 9])
+def test_bulb_de_brackets_axis_distance(orc, n):
+    """The set meets the +y axis in [0, y*], y* the largest y0 whose orbit of 0
+    under y <- y^n + y0 stays bounded (found here by bisection on the real map).
+    The distance from (0, y0, 0) to the set is therefore at most y0 - y*, and the
+    DE, a lower bound on that distance (Sec. 2), may not exceed it.  There is no
+    theorem for a lower bracket in 3D; over this sweep (y0 - y*) / DE stays in
+    [1.6, 32] for every power, and the test holds it inside [1, 40]."""
+    s = W.bulb_1080p(0, 8, 8)
+    s["n"] = n
+
+    def bounded(c):
+        y = 0.0
+        for _ in range(20000):
+            y = y**n + c
+            if y > 2.0:
+                return False
+        return True
+
+    lo, hi = 0.0, 2.0
+    for _ in range(50):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if bounded(mid) else (lo, mid)
+    y_star = hi
+    ys = np.linspace(y_star + 1e-3, 2.0, 200)
+    d, _, _, _ = orc.de(s, np.stack([0 * ys, ys, 0 * ys], 1))
+    gap = ys - y_star
+    assert np.all(d <= gap)
+    pos = d > 0  # just outside y*, 12 steps do not tell the orbit from a bounded one
+    assert pos.mean() > 0.9
+    ratio = gap[pos] / d[pos]
+    assert ratio.min() >= 1.0 and ratio.max() <= 40.0, (ratio.min(), ratio.max())
+
+
 # ------------------------------------------------------ analytic normal (Sec. 2)
 @pytest.mark.parametrize("p", [2, 3])
 def test_analytic_normal_reduces_to_complex_derivative(orc, p):
