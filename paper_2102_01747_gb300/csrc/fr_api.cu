@@ -230,6 +230,36 @@ fr_status launched(cudaError_t e)
 namespace fr {
 // error reporting for entry points defined in other translation units
 fr_status set_error(fr_status st, const char *msg) { return fail(st, "%s", msg); }
+
+// Checks every request of a batch and resolves it into all[i] (no CUDA call);
+// count is set when some request asks for the statistics counters.  The
+// message of the first bad request names its index.
+fr_status resolve_requests(const fr_request *reqs, int n_reqs, std::vector<DevReq> &all, bool &count)
+{
+    if (!reqs) return fail(FR_EINVAL, "requests is NULL");
+    if (n_reqs < 1 || n_reqs > 4096) return fail(FR_EINVAL, "n_reqs %d outside 1..4096", n_reqs);
+    all.assign((size_t)n_reqs, DevReq{});
+    count = false;
+    for (int i = 0; i < n_reqs; i++) {
+        DevReq &R = all[(size_t)i];
+        std::memset(&R, 0, sizeof R);
+        const fr_request &q = reqs[i];
+        fr_status st;
+        if (q.kind == FR_KIND_JULIA)
+            st = resolve_julia(R, &q.julia);
+        else if (q.kind == FR_KIND_BULB)
+            st = resolve_bulb(R, &q.bulb);
+        else
+            st = fail(FR_EINVAL, "kind %d unknown", q.kind);
+        if (st == FR_OK) st = resolve_common(R, &q.plane, &q.camera, &q.light, &q.out);
+        if (st != FR_OK) {
+            g_err = "request " + std::to_string(i) + ": " + g_err;
+            return st;
+        }
+        count = count || q.out.stats != nullptr;
+    }
+    return FR_OK;
+}
 }  // namespace fr
 
 extern "C" {
@@ -343,25 +373,11 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         return fail(FR_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, fr_batch_workspace_bytes(n_reqs));
     // check every request before launching anything
     static thread_local fr::BatchArgs A;
-    std::vector<fr::DevReq> all((size_t)n_reqs);
+    std::vector<fr::DevReq> all;
     bool count = false;
-    for (int i = 0; i < n_reqs; i++) {
-        fr::DevReq &R = all[(size_t)i];
-        std::memset(&R, 0, sizeof R);
-        const fr_request &q = reqs[i];
-        fr_status st;
-        if (q.kind == FR_KIND_JULIA)
-            st = resolve_julia(R, &q.julia);
-        else if (q.kind == FR_KIND_BULB)
-            st = resolve_bulb(R, &q.bulb);
-        else
-            st = fail(FR_EINVAL, "kind %d unknown", q.kind);
-        if (st == FR_OK) st = resolve_common(R, &q.plane, &q.camera, &q.light, &q.out);
-        if (st != FR_OK) {
-            g_err = "request " + std::to_string(i) + ": " + g_err;
-            return st;
-        }
-        count = count || q.out.stats != nullptr;
+    {
+        const fr_status st = fr::resolve_requests(reqs, n_reqs, all, count);
+        if (st != FR_OK) return st;
     }
     const fr_tuning tu = tuning();
 

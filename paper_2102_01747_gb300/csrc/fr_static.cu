@@ -9,19 +9,25 @@
 // Every GPU that loads the library holds the array until the process exits.
 //
 // Host code must not hand the array's name to a kernel: on the host it is only
-// a stand-in symbol.  Its device address is looked up once per device with
-// cudaGetSymbolAddress (on the first call made with that device current) and
-// kept.  The batch itself then goes through the unchanged fr_render_batch,
-// which zeroes each queue head with a memset on the stream before its launch,
-// so what the previous call left in the array does not matter.
+// a stand-in symbol.  Its device address comes from cudaGetSymbolAddress with
+// the device current, on every call made outside a stream capture (so a
+// context that was reset and re-created, which maps the array anew, is
+// followed), and the last address seen on each device is kept for calls made
+// while their stream is being captured, when no such lookup may run.  The
+// batch itself then goes through the unchanged fr_render_batch, which zeroes
+// each queue head with a memset on the stream before its launch, so what the
+// previous call left in the array does not matter.
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include "../../include/fr.h"
+#include "fr_launch.h"
 
 namespace fr {
 fr_status set_error(fr_status st, const char *msg);
+fr_status resolve_requests(const fr_request *reqs, int n_reqs, std::vector<DevReq> &all, bool &count);
 }
 
 namespace {
@@ -43,29 +49,51 @@ extern "C" {
 FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, void *stream)
 {
     char msg[160];
+    if (!reqs) return fr::set_error(FR_EINVAL, "requests is NULL");
     if (n_reqs < 1 || n_reqs > kStaticMaxRequests) {
         snprintf(msg, sizeof msg, "n_reqs %d outside 1..%d (the static workspace holds %d launches)",
                  n_reqs, kStaticMaxRequests, kStaticLaunches);
         return fr::set_error(FR_EINVAL, msg);
     }
+    {
+        // every request is checked before the first CUDA call (which may create
+        // the context); fr_render_batch checks them again, on the host only
+        std::vector<fr::DevReq> all;
+        bool count = false;
+        const fr_status st = fr::resolve_requests(reqs, n_reqs, all, count);
+        if (st != FR_OK) return st;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
+        cudaGetLastError();  // leave no error behind for the next launch check
         snprintf(msg, sizeof msg, "cudaGetDevice failed: %s", cudaGetErrorString(e));
         return fr::set_error(FR_ECUDA, msg);
     }
     if (dev < 0 || dev >= kMaxDevices) return fr::set_error(FR_EINVAL, "device ordinal beyond 63");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // leave no error behind for the next launch check
+        snprintf(msg, sizeof msg, "cudaStreamIsCapturing failed: %s", cudaGetErrorString(e));
+        return fr::set_error(FR_ECUDA, msg);
+    }
     void *ws = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_static_mu);
-        ws = g_static_addr[dev];
-        if (!ws) {
+        if (cap == cudaStreamCaptureStatusNone) {
             e = cudaGetSymbolAddress(&ws, g_static_ws);
             if (e != cudaSuccess || !ws) {
-                snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+                cudaGetLastError();  // leave no error behind for the next launch check
+            snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
                 return fr::set_error(FR_ECUDA, msg);
             }
             g_static_addr[dev] = ws;
+        } else {
+            ws = g_static_addr[dev];
+            if (!ws)
+                return fr::set_error(FR_EINVAL, "the first fr_render_batch_static call on a device must come "
+                                                "before any stream capture (it looks up the array's address)");
         }
     }
     return fr_render_batch(reqs, n_reqs, ws, kStaticBytes, stream);

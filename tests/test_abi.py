@@ -320,3 +320,23 @@ def test_c_client_compiles_against_the_header():
     with tempfile.TemporaryDirectory() as d:
         exe = c_client_build.build(d)
         assert os.path.exists(exe)
+
+
+def test_static_batch_checks_requests_before_any_cuda_call(F):
+    """fr_render_batch_static refuses a NULL request array, a count outside
+    1..4096 and a bad request on the host, before it asks CUDA for the device
+    or the array's address (here there is no GPU, so any CUDA call would fail
+    with FR_ECUDA instead)."""
+    lib = F.load()
+    assert lib.fr_render_batch_static(None, 3, None) == F.FR_EINVAL
+    assert "NULL" in F.fr_last_error()
+    s = W.julia_256(16, 16)
+    req = F.fr_request()
+    req.kind = F.FR_KIND_JULIA
+    req.julia, req.plane, req.camera, req.light = _structs(s)
+    arr = (F.fr_request * 2)(req, req)  # no output buffer in either request
+    assert F.fr_render_batch_static(arr, 2, None) == F.FR_EINVAL
+    assert "request 0" in F.fr_last_error() and "no output" in F.fr_last_error()
+    arr[0].julia.p = 5
+    assert F.fr_render_batch_static(arr, 2, None) == F.FR_EINVAL
+    assert "request 0" in F.fr_last_error() and "degree" in F.fr_last_error()

@@ -85,18 +85,24 @@ def test_batch_graph(env, batch_kernel):
         F.fr_set_tuning(old)
 
 
-def test_static_batch_graph(env):
-    """The allocation-free batch call: its first (eager) call looks up the device
-    array's address; captured afterwards, it replays like the others."""
+@pytest.mark.parametrize("batch_kernel, n_requests", [(1, 5), (0, 70)])
+def test_static_batch_graph(env, batch_kernel, n_requests):
+    """The allocation-free batch call: its eager call looks up the device array's
+    address; captured afterwards, it replays like the others.  Under the
+    persistent schedule (which reads the queue heads in the array) 70 requests
+    make two launches, using two slots of the array."""
     torch, F, api = env
-    scenes = W.batch_mixed(seed=8, n_requests=5, min_log2=4.0, max_log2=6.0)
+    scenes = W.batch_mixed(seed=8, n_requests=n_requests, min_log2=4.0, max_log2=6.0)
     outs = [api.alloc_image(s, rgba8=True, depth=True) for s in scenes]
     arr = api.request_array(scenes, outs)
+    old = _tuned(F, batch_kernel=batch_kernel)
+    try:
+        def call(s):
+            F.check(F.fr_render_batch_static(arr, len(scenes), s.cuda_stream))
 
-    def call(s):
-        F.check(F.fr_render_batch_static(arr, len(scenes), s.cuda_stream))
-
-    _replay_matches_eager(torch, outs, call)
+        _replay_matches_eager(torch, outs, call)
+    finally:
+        F.fr_set_tuning(old)
     # and the images are the per-request kernel's
     for sc, o in zip(scenes, outs):
         ref = api.render(sc, rgba8=True, depth=True)
