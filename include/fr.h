@@ -268,9 +268,12 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
  * break frame pacing).  The queue heads live in a 16 KB file-scope __device__
  * array of the library, enough for the largest batch fr_render_batch accepts
  * (4096 requests); every GPU that loads the library keeps it until exit.  The
- * first call on a device looks the array's address up (cudaGetSymbolAddress)
- * with that device current, so make that first call before any stream
- * capture.  Nothing is allocated: no cudaMalloc, cudaFree or allocating
+ * requests are checked before any CUDA call.  A call made while `stream` is not
+ * being captured looks the array's address up (cudaGetSymbolAddress, with the
+ * current device), so a device reset in between is followed; a call made
+ * during a stream capture reuses the address last looked up on that device,
+ * so the first call on a device must come before any capture (otherwise
+ * FR_EINVAL).  Nothing is allocated: no cudaMalloc, cudaFree or allocating
  * library call.  The array is shared by every call (each launch zeroes its own
  * queue head first), so calls that overlap on the GPU -- on different streams,
  * or from different threads -- race on it; serialise them.  Errors: as
