@@ -33,17 +33,45 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # everything included (orbit step, DE epilogue, march update, stencils, camera
 # ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
 # divided by the iterations counted on the same scene (Mandelbulb n = 8 at
-# 1920x1080: 8.534 G / 50.88 M = 167.7, profiles/plain_kernel_mandelbulb_1080p.md;
-# Julia p = 2 at 256x256: 364.9 M / 10.27 M = 35.6).  The degree-3 Julia figure
-# is the degree-2 one scaled by the ratio of their orbit-step arithmetic
-# (28 / 24); other Mandelbulb powers take the n = 8 figure (same calls per step).
+# 1920x1080: 8.534 G / 50.88 M = 167.7; Julia p = 2 at 256x256:
+# 364.9 M / 10.27 M = 35.6).  The degree-3 Julia figure is the degree-2 one
+# scaled by the ratio of their orbit-step arithmetic (28 / 24); other
+# Mandelbulb powers take the n = 8 figure (same calls per step).
 FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5, ("bulb", 8): 167.7}
+# The algorithmic count of the same work: the operations of the listings'
+# formulas as written, each math-library call (sqrt, pow, acos, atan2, sin,
+# cos, log) counted as one operation, nothing for the library's internals.
+# Per orbit iteration: Julia p = 2, dz2 *= 4 m2 (2), z^2 + c (15), m2 (7);
+# p = 3, dz2 *= 9 m2^2 (3), z^3 + c (18), m2 (7); Mandelbulb, r = sqrt(m) (1),
+# dz = n r^(n-1) dz + 1 (4 with the pow), b = n acos(y/r) (3),
+# a = n atan2(x, z) (2), two sines and two cosines (4), r^n (1), the point
+# r^n (sin b sin a, cos b, sin b cos a) + c (8), m = |w|^2 (5).  Per DE call:
+# the march point ro + t rd (6), the start |p|^2 (Julia 7, Mandelbulb 5), the
+# distance 0.25 log(m) sqrt(...) (Julia 5, Mandelbulb 5) and the step
+# t += min(d, max_step) (1).
+ALG_PER_ITER = {("julia", 2): 24, ("julia", 3): 28, "bulb": 29}
+ALG_PER_DE = {"julia": 19, "bulb": 17}
 # DRAM bytes of one launch of the dominant kernel (by the kernel the tuned
 # configuration launches), from the ncu capture of the same command
 # (dram__bytes_read.sum + dram__bytes_write.sum); the frame's 16.6 MB of
 # stores are still in the 129 MB L2 when the kernel ends.
 TRAFFIC = {("bulb_1080p", "plain_kernel"): 1390080 + 29952, ("bulb_1080p", "batch_plain_kernel"): 70400 + 1024}
-FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32)
+# The kernel sources the two tables above were counted on (sha256 over these
+# files in this order): when the sources change, the bench reports the
+# figures as stale and the traffic as null until they are counted again.
+COUNTED_SOURCES = ("fr_device.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
+COUNTED_SHA = "16bdc8a17eab79a0f5d64339e67b33bf021538fbc75b53b4083388c68070667d"
+FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
+
+
+def kernel_sources_sha() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in COUNTED_SOURCES:
+        with open(os.path.join(ROOT, "paper_2102_01747_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def workload(name: str, rank: int = 0):
@@ -88,6 +116,13 @@ def flops_per_iter(scene) -> float:
     return FLOPS_PER_ITER.get(key, FLOPS_PER_ITER[("bulb", 8)] if scene["kind"] == "bulb" else 35.6)
 
 
+def alg_flops(scene, counts) -> float:
+    """Algorithmic FP32 operations of one render of `scene` from its counters."""
+    it = ALG_PER_ITER[("julia", scene["p"])] if scene["kind"] == "julia" else ALG_PER_ITER["bulb"]
+    de = counts[2] + counts[3] + counts[4] + counts[7]
+    return it * counts[5] + ALG_PER_DE[scene["kind"]] * de
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -130,10 +165,6 @@ class ClockSampler:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
-
-
-def fp32_peak_tflops(clock_mhz: float, sms: int) -> float:
-    return sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
 
 
 def _stride_words(stride):
@@ -281,30 +312,158 @@ def max_over_ranks(torch, dist, seconds: float, device) -> float:
     return float(t.item())
 
 
-def count_frame(api, torch, scenes):
-    """Counting-kernel pass (untimed): summed FR_STAT_* counters of all scenes."""
+def count_scenes(api, torch, scenes):
+    """Counting-kernel pass (untimed): the FR_STAT_* counters of each scene."""
     from paper_2102_01747_gb300 import _ffi as F
 
-    tot = [0] * F.FR_NSTATS
+    per = []
     for s in scenes:
         c = api.render(s, rgba8=False, depth=False, stats=True)
         torch.cuda.synchronize()
-        for k, v in enumerate(c["stats"].cpu().tolist()):
-            tot[k] += int(v)
-    return tot
+        per.append([int(v) for v in c["stats"].cpu().tolist()][:F.FR_NSTATS])
+    return per
 
 
-def flops_of(scenes, per_scene_iters):
-    return sum(flops_per_iter(s) * it for s, it in zip(scenes, per_scene_iters))
+def _sum_counts(per):
+    return [sum(c[k] for c in per) for k in range(len(per[0]))]
 
 
-def run_gradient(args, torch, api, F, scenes, desc, rank, world):
+def rays_of(c):
+    return c[0] + c[1] + c[6]  # camera, shadow and mirror rays
+
+
+def des_of(c):
+    return c[2] + c[3] + c[4] + c[7]
+
+
+def fp32_peak_tflops(clock_mhz: float, sms: int) -> float:
+    return sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+
+
+def ffma_probe(torch, F, dev, sms: int, seconds: float = 0.05, reps: int = 5) -> dict:
+    """The FP32 FFMA rate of this GPU (fr_ffma_probe): 8 blocks of 256 threads per
+    SM, each thread 8 independent FFMA chains, launches of about `seconds`;
+    the fastest of `reps` timed launches (a burst, like the kernels it is the
+    denominator for), with the clocks sampled meanwhile."""
+    blocks, threads = sms * 8, 256
+    iters = max(1, int(seconds * 80e12 / F.fr_ffma_probe_flops(blocks, threads, 1)))
+    sink = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def launch():
+        F.check(F.fr_ffma_probe(blocks, threads, iters, sink.data_ptr(), stream.cuda_stream))
+
+    for _ in range(2):
+        launch()
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(dev.index or 0) as clk:
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            launch()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    c = clk.summary()
+    flops = F.fr_ffma_probe_flops(blocks, threads, iters)
+    tflops = flops / (min(ms) / 1e3) / 1e12
+    mhz = c.get("sm_mhz") or 2070.0
+    return {"tflops": tflops, "ms_per_launch": min(ms), "launch": [blocks, threads, iters],
+            "flops_per_launch": flops, "clocks": c,
+            "ffma_lanes_per_sm": tflops * 1e12 / (sms * 2 * mhz * 1e6)}
+
+
+def roofline_of(flops_ncu, flops_alg, kernel_ms, launches, peak, peak_derived, traffic, kern):
+    achieved = flops_ncu / launches / (kernel_ms / 1e3) / 1e12
+    achieved_alg = flops_alg / launches / (kernel_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kern,
+            "achieved_algorithmic": achieved_alg, "frac_algorithmic": achieved_alg / peak,
+            "frac_of_derived_peak": achieved / peak_derived}
+
+
+def measure(args, torch, api, F, scenes, path, env, steps, warmup, clk_index=None, tune=True, tune_reps=3,
+            compare=True, dist=None, world=1):
+    """Counters, an optional untimed autotuner search, then `steps` timed steps of
+    the scenes through `path` (and through the other path when `compare`).
+    Returns the measurement and the tuning the autotuner left applied."""
+    dev, tstream, flush = env["dev"], env["tstream"], env["flush"]
+    stream = api.current_stream(dev)
+    tuning = None
+    if tune and path == "batch":
+        from paper_2102_01747_gb300 import autotune
+
+        space = dict(autotune.SPACE)
+        if args.batch_kernel is not None:
+            del space["batch_kernel"]
+        if args.tile_order is not None:
+            del space["tile_order"]
+        r = autotune.tune(scenes, reps=tune_reps, space=space)  # untimed search over the launch shape
+        tuning = {"config": r["config"], "search_ms": r["ms"], "trials": len(r["trials"])}
+    elif tune and path == "plain" and len(scenes) == 1:
+        from paper_2102_01747_gb300 import autotune
+
+        space = dict(autotune.SINGLE_SPACE)
+        if args.tile_order is not None:
+            del space["tile_order"]
+        if args.single_kernel is not None:
+            del space["single_kernel"]
+        r = autotune.tune_single(scenes[0], reps=max(tune_reps, 3), space=space, start_kernel=args.single_kernel)
+        tuning = {"config": r["config"], "search_ms": r["ms"], "trials": len(r["trials"]),
+                  "trial_ms": [[{k: t[k] for k in space}, round(t["ms"], 4)] for t in r["trials"]]}
+    per = count_scenes(api, torch, scenes)
+    tot = _sum_counts(per)
+    flops_ncu = sum(flops_per_iter(s) * c[5] for s, c in zip(scenes, per))
+    flops_alg = sum(alg_flops(s, c) for s, c in zip(scenes, per))
+    outs = [api.alloc_image(s, rgba8=True, depth=True) for s in scenes]
+    paths = [path] + ([p for p in ("plain", "batch") if p != path] if compare else [])
+    results = {}
+    for pth in paths:
+        step = Renderer(api, F, scenes, outs, pth, stream)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        times, total_s, clk = time_steps(torch, step, steps, tstream, flush, dist,
+                                         clk_index=clk_index if pth == path else None)
+        results[pth] = {"times": times, "total_s": total_s, "clk": clk, "launches": step.launches()}
+    tu = F.fr_get_tuning()
+    if path == "plain":  # the kernel fr_render_* launches under the tuned single_kernel
+        kern = {0: "plain_kernel", 1: "persist_kernel", 2: "batch_plain_kernel"}[tu.single_kernel]
+    else:
+        kern = "batch_plain_kernel" if tu.batch_kernel == 1 else "persist_kernel"
+    main_r = results[path]
+    return {"per": per, "counts": tot, "flops_ncu": flops_ncu, "flops_alg": flops_alg, "outs": outs,
+            "results": results, "main": main_r, "kernel": kern, "tuning": tuning,
+            "value": rays_of(tot) * steps * world / main_r["total_s"] / 1e6,
+            "kernel_ms": statistics.mean(main_r["times"]) / main_r["launches"]}
+
+
+def summary_of(m, steps, peak, peak_derived, traffic=None, world=1):
+    """The compact record of a measurement (for the extras)."""
+    total_s = m["main"]["total_s"]
+    out = {"ms_per_step": total_s / steps * 1e3, "value": m["value"], "unit": "Mrays/s",
+           "rays_per_step": rays_of(m["counts"]), "de_calls_per_step": des_of(m["counts"]),
+           "orbit_iters_per_step": m["counts"][5],
+           "de_evals_per_s": des_of(m["counts"]) * steps * world / total_s,
+           "roofline": roofline_of(m["flops_ncu"], m["flops_alg"], m["kernel_ms"], m["main"]["launches"], peak,
+                                   peak_derived, traffic, m["kernel"])}
+    for pth, r in m["results"].items():
+        if r is not m["main"]:
+            out["other_path"] = {"path": pth, "ms_per_step": r["total_s"] / steps * 1e3,
+                                 "launches_per_step": r["launches"]}
+            out["speedup_vs_" + pth] = r["total_s"] / total_s
+    if m["tuning"]:
+        out["tuning"] = {k: v for k, v in m["tuning"].items() if k != "trial_ms"}
+    return out
+
+
+def measure_gradient(args, torch, api, F, scene, steps, warmup):
     """One step = a differentiable Julia render (colour, depth, saved hit state) plus
     the adjoint (fr_render_backward) of an L2 loss: gradients per second.  The
     finite-difference alternative needs 22 forward renders per gradient (central
     differences over c[4], plane n[3], offset, light[3])."""
-    s = scenes[0]
-    H, Wd = s["camera"]["height"], s["camera"]["width"]
+    s = scene
     out = api.alloc_image(s, rgba8=False, rgba=True, depth=True, saved=True)
     target = api.render(s, rgba8=False, rgba=True, depth=False)["rgba"].clone()
     grad = torch.zeros(11, dtype=torch.float32, device="cuda")
@@ -323,32 +482,38 @@ def run_gradient(args, torch, api, F, scenes, desc, rank, world):
         F.check(F.fr_render_backward(prm, pl, cam, li, out["saved"].data_ptr(), d_rgba.data_ptr(),
                                      None, grad.data_ptr(), stream))
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     tstream = torch.cuda.current_stream()
-    times, total_s, clk = time_steps(torch, step, args.steps, tstream, flush, None, clk_index=0)
-    ftimes, ftotal, _ = time_steps(torch, forward, args.steps, tstream, flush, None)
-    grad_per_s = args.steps / total_s
-    fd_per_s = 1.0 / (22 * ftotal / args.steps)
+    times, total_s, clk = time_steps(torch, step, steps, tstream, flush, None, clk_index=0)
+    ftimes, ftotal, _ = time_steps(torch, forward, steps, tstream, flush, None)
+    grad_per_s = steps / total_s
+    fd_per_s = 1.0 / (22 * ftotal / steps)
     e2e_t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
         grad.cpu()
-    e2e = args.steps / (time.perf_counter() - e2e_t0)
+    e2e = steps / (time.perf_counter() - e2e_t0)
+    return {"value": grad_per_s, "unit": "grad/s", "ms_per_step": total_s / steps * 1e3,
+            "forward_ms": ftotal / steps * 1e3, "fd_grad_per_s": fd_per_s, "speedup_vs_fd": grad_per_s / fd_per_s,
+            "e2e": {"value": e2e, "unit": "grad/s", "h2d_bytes_per_step": ctypes_sizeof_inputs(F, 1),
+                    "d2h_bytes_per_step": 44},
+            "clocks": clk, "width": s["camera"]["width"], "height": s["camera"]["height"]}
+
+
+def run_gradient(args, torch, api, F, scenes, desc, rank, world):
+    g = measure_gradient(args, torch, api, F, scenes[0], args.steps, args.warmup)
     if rank != 0:
         return
     print(json.dumps({
-        "metric": "grad/s", "value": grad_per_s, "unit": "grad/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
+        "metric": "grad/s", "value": g["value"], "unit": "grad/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": g["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": {"workload": desc, "width": Wd, "height": H,
+        "data": "synthetic", "config": {"workload": desc, "width": g["width"], "height": g["height"],
                                         "l2": "flushed between timed steps (256 MB write)"},
-        "forward_ms": ftotal / args.steps * 1e3,
-        "fd_grad_per_s": fd_per_s, "speedup_vs_fd": grad_per_s / fd_per_s,
-        "e2e": {"value": e2e, "unit": "grad/s", "h2d_bytes_per_step": ctypes_sizeof_inputs(F, 1),
-                "d2h_bytes_per_step": 44},
-        "gpu_launches": 2 * args.steps, "clocks": clk,
+        "forward_ms": g["forward_ms"], "fd_grad_per_s": g["fd_grad_per_s"], "speedup_vs_fd": g["speedup_vs_fd"],
+        "e2e": g["e2e"], "gpu_launches": 2 * args.steps, "clocks": g["clocks"],
     }))
 
 
@@ -408,6 +573,8 @@ def main():
                          "request, batch for several")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other path")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the other configurations and the FFMA probe")
     ap.add_argument("--no-autotune", action="store_true", help="keep the current launch shape")
     ap.add_argument("--single-kernel", type=int, choices=(0, 1, 2), default=None,
                     help="fix the kernel of fr_render_julia / fr_render_mandelbulb (0 single-request "
@@ -454,7 +621,6 @@ def main():
         if args.tile_order is not None:
             t.tile_order = args.tile_order
         F.check(F.fr_set_tuning(t))
-    stream = api.current_stream(dev)
     tstream = torch.cuda.current_stream(dev)
     if args.path == "auto":
         # the animation renders its frames one call each
@@ -464,59 +630,18 @@ def main():
     if args.workload == "stress_anim":
         return run_animation(args, torch, api, F, desc, rank, world)
 
-    tuning = None
-    if args.path == "batch" and not args.no_autotune:
-        from paper_2102_01747_gb300 import autotune
+    env = {"dev": dev, "tstream": tstream,
+           "flush": torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)}  # > 129 MB L2
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    extras = args.workload == "bulb_1080p" and not args.no_extras and world == 1
+    probe = ffma_probe(torch, F, dev, sms) if extras else None
 
-        space = dict(autotune.SPACE)
-        if args.batch_kernel is not None:
-            del space["batch_kernel"]
-        if args.tile_order is not None:
-            del space["tile_order"]
-        tuning = autotune.tune(scenes, reps=3, space=space)  # untimed search over the launch shape
-        tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"])}
-    elif args.path == "plain" and len(scenes) == 1 and not args.no_autotune:
-        from paper_2102_01747_gb300 import autotune
-
-        space = dict(autotune.SINGLE_SPACE)
-        if args.tile_order is not None:
-            del space["tile_order"]
-        if args.single_kernel is not None:
-            del space["single_kernel"]
-        tuning = autotune.tune_single(scenes[0], space=space, start_kernel=args.single_kernel)
-        tuning = {"config": tuning["config"], "search_ms": tuning["ms"], "trials": len(tuning["trials"]),
-                  "trial_ms": [[{k: t[k] for k in space}, round(t["ms"], 4)] for t in tuning["trials"]]}
-
-    counts = count_frame(api, torch, scenes)
-    per_scene_iters = []
-    if len(scenes) > 1:
-        for s in scenes:
-            per_scene_iters.append(count_frame(api, torch, [s])[5])
-    else:
-        per_scene_iters = [counts[5]]
-    rays_per_step = counts[0] + counts[1] + counts[6]  # camera, shadow and mirror rays
-    de_per_step = counts[2] + counts[3] + counts[4] + counts[7]
-    iters_per_step = counts[5]
-    flops_per_step = flops_of(scenes, per_scene_iters)
-
-    outs = [api.alloc_image(s, rgba8=True, depth=True) for s in scenes]
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-
-    paths = [args.path] + ([] if args.no_compare else [p for p in ("plain", "batch") if p != args.path])
-    results = {}
-    for path in paths:
-        step = Renderer(api, F, scenes, outs, path, stream)
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        times, total_s, clk = time_steps(torch, step, args.steps, tstream, flush, dist,
-                                         clk_index=local if path == args.path else None)
-        results[path] = {"times": times, "total_s": total_s, "clk": clk, "launches": step.launches()}
-
-    main_r = results[args.path]
+    m = measure(args, torch, api, F, scenes, args.path, env, args.steps, args.warmup, clk_index=local,
+                tune=not args.no_autotune, tune_reps=9, compare=not args.no_compare, dist=dist, world=world)
+    main_r, outs = m["main"], m["outs"]
     total_s = main_r["total_s"]
-    value = rays_per_step * args.steps * world / total_s / 1e6
-    kernel_ms = statistics.mean(main_r["times"]) / main_r["launches"]
+    counts = m["counts"]
+    rays_per_step = rays_of(counts)
 
     # end to end through the public API with host buffers: the scene parameters go
     # in with the call, every image (rgba8 + depth) comes back to pinned memory.
@@ -570,22 +695,31 @@ def main():
     in_bytes = ctypes_sizeof_inputs(F, len(scenes))
     out_bytes = sum(o["rgba8"].numel() * 4 + o["depth"].numel() * 4 for o in outs)
 
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
     c = main_r["clk"] or {}
     max_mhz = c.get("sm_max_mhz") or 2070.0
-    peak = fp32_peak_tflops(max_mhz, sms)
-    achieved = flops_per_step / main_r["launches"] / (kernel_ms / 1e3) / 1e12
+    peak_derived = fp32_peak_tflops(max_mhz, sms)
+    peak = probe["tflops"] if probe else peak_derived
+    fresh = kernel_sources_sha() == COUNTED_SHA
+    traffic = TRAFFIC.get((args.workload, m["kernel"])) if fresh else None
+    roof = roofline_of(m["flops_ncu"], m["flops_alg"], m["kernel_ms"], main_r["launches"], peak, peak_derived,
+                       traffic, m["kernel"])
+    roof.update({
+        "flops_per_step": m["flops_ncu"], "flops_per_step_algorithmic": m["flops_alg"],
+        "per_unit_figures_current": fresh,
+        "peak_basis": ("measured: FFMA probe (fr_ffma_probe), fastest of 5 launches of %.0f ms" %
+                       probe["ms_per_launch"]) if probe else
+                      "derived: %d SMs x %d lanes x 2 flops x %.0f MHz (max clock)" % (sms, FP32_LANES_PER_SM, max_mhz),
+        "peak_derived": peak_derived,
+        "peak_derived_basis": "%d SMs x %d FFMA lanes x 2 flops x %.0f MHz (max clock)" % (
+            sms, FP32_LANES_PER_SM, max_mhz),
+        "frac_at_observed_clock": (m["flops_ncu"] / main_r["launches"] / (m["kernel_ms"] / 1e3) / 1e12 /
+                                   fp32_peak_tflops(c["sm_mhz"], sms)) if c.get("sm_mhz") else None,
+    })
 
     if rank != 0:
         return
-    tu = F.fr_get_tuning()
-    if args.path == "plain":  # the kernel fr_render_* launches under the tuned single_kernel
-        kern = {0: "plain_kernel", 1: "persist_kernel", 2: "batch_plain_kernel"}[tu.single_kernel]
-    else:
-        kern = "batch_plain_kernel" if tu.batch_kernel == 1 else "persist_kernel"
     res = {
-        "metric": "Mrays/s", "value": value, "unit": "Mrays/s",
+        "metric": "Mrays/s", "value": m["value"], "unit": "Mrays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -593,18 +727,11 @@ def main():
                    "pixels_per_step": sum(s["camera"]["width"] * s["camera"]["height"] for s in scenes),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas (one frame per rank)" if world > 1 else "single GPU"},
-        "de_evals_per_s": de_per_step * args.steps * world / total_s,
-        "orbit_iters_per_s": iters_per_step * args.steps * world / total_s,
+        "de_evals_per_s": des_of(counts) * args.steps * world / total_s,
+        "orbit_iters_per_s": counts[5] * args.steps * world / total_s,
         "per_step": {"rays": rays_per_step, "primary_rays": counts[0], "shadow_rays": counts[1],
-                     "mirror_rays": counts[6], "de_calls": de_per_step, "orbit_iters": iters_per_step},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, kern)),
-                     "kernel": kern,
-                     "flops_per_step": flops_per_step,
-                     "peak_basis": "FP32 FFMA: %d SMs x %d lanes x 2 flops x %.0f MHz (max clock)" % (
-                         sms, FP32_LANES_PER_SM, max_mhz),
-                     "frac_at_observed_clock": (achieved / fp32_peak_tflops(c["sm_mhz"], sms))
-                     if c.get("sm_mhz") else None},
+                     "mirror_rays": counts[6], "de_calls": des_of(counts), "orbit_iters": counts[5]},
+        "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "Mrays/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": out_bytes, "serial_value": e2e_serial,
                 "note": "inputs are the scene parameter structs passed in each call; value: the copy of "
@@ -612,61 +739,79 @@ def main():
                         "buffers, a copy stream); serial_value: render, copy, wait every step"},
         "gpu_launches": main_r["launches"] * args.steps,
         "clocks": c,
-        "tuning": tuning,
+        "tuning": m["tuning"],
     }
-    for path, r in results.items():
+    for path, r in m["results"].items():
         if path != args.path:
             res["other_path"] = {"path": path,
                                  "value": rays_per_step * args.steps * world / r["total_s"] / 1e6,
                                  "ms_per_step": r["total_s"] / args.steps * 1e3}
             res["speedup_vs_" + path] = r["total_s"] / total_s
-    if args.workload == "bulb_1080p" and not args.no_compare:
-        res["extras"] = bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step)
+    if extras:
+        res["extras"] = bulb_extras(args, torch, api, F, scenes, env, peak, peak_derived)
+        res["extras"]["ffma_probe"] = probe
+        res["extras"].update(other_configs(args, torch, api, F, env, peak, peak_derived))
     if world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(scenes)
     print(json.dumps(res))
 
 
-def bulb_extras(args, torch, api, F, scenes, outs, flush, tstream, rays_per_step):
-    """More views of the same frame: (1) Eq. 1 evaluated without
-    transcendental calls (de Moivre powers; same image within the parity bar);
-    (2) the analytic normal in place of the tetrahedral stencil; (3) with the
-    orbit-trap output; (4) eight consecutive frames of the camera orbit in one
-    fr_render_batch call, where one frame's slowest pixels overlap the other
-    frames' work."""
+def bulb_extras(args, torch, api, F, scenes, env, peak, peak_derived):
+    """More views of the same frame, each timed like the headline (CUDA events,
+    L2 flushed): (1) Eq. 1 evaluated without transcendental calls (de Moivre
+    powers; same image within the parity bar); (2) the analytic normal in place
+    of the tetrahedral stencil; (3) with the orbit-trap output; (4) eight
+    consecutive frames of the camera orbit in one fr_render_batch call, where
+    one frame's slowest pixels overlap the other frames' work (the steady state
+    of an animation)."""
     out = {}
+    n = max(5, args.steps // 2)
+    w = 3
     alg = [dict(s, algebraic=True) for s in scenes]
-    counts = count_frame(api, torch, alg)
-    step = Renderer(api, F, alg, outs, "plain", api.current_stream())
-    for _ in range(args.warmup):
+    for name, sc in (("algebraic_power", alg), ("analytic_normal", [dict(s, normal_mode="analytic") for s in scenes])):
+        mm = measure(args, torch, api, F, sc, "plain", env, n, w, tune=False, compare=False)
+        out[name] = dict(summary_of(mm, n, peak, peak_derived), path="plain")
+    # the orbit-trap output (one more DE per hit pixel)
+    per = count_scenes(api, torch, scenes)
+    oo = [api.alloc_image(s, trap=True) for s in scenes]
+    step = Renderer(api, F, scenes, oo, "plain", api.current_stream())
+    for _ in range(w):
         step()
-    times, total, _ = time_steps(torch, step, args.steps, tstream, flush)
-    out["algebraic_power"] = {"path": "plain", "ms_per_frame": total / args.steps * 1e3,
-                              "value": (counts[0] + counts[1] + counts[6]) * args.steps / total / 1e6,
-                              "unit": "Mrays/s", "orbit_iters": counts[5]}
-    # the analytic normal (one orbit carrying its Jacobian per hit, in place of
-    # the four stencil DEs) and the orbit-trap output (one more DE per hit pixel)
-    for name, sc, oo in (("analytic_normal", [dict(s, normal_mode="analytic") for s in scenes], outs),
-                         ("orbit_trap", scenes, [api.alloc_image(s, trap=True) for s in scenes])):
-        c = count_frame(api, torch, sc)
-        step = Renderer(api, F, sc, oo, "plain", api.current_stream())
-        for _ in range(args.warmup):
-            step()
-        times, total, _ = time_steps(torch, step, args.steps, tstream, flush)
-        out[name] = {"path": "plain", "ms_per_frame": total / args.steps * 1e3,
-                     "value": (c[0] + c[1] + c[6]) * args.steps / total / 1e6, "unit": "Mrays/s",
-                     "orbit_iters": c[5]}
+    times, total, _ = time_steps(torch, step, n, env["tstream"], env["flush"])
+    out["orbit_trap"] = {"path": "plain", "ms_per_step": total / n * 1e3,
+                         "value": rays_of(_sum_counts(per)) * n / total / 1e6, "unit": "Mrays/s"}
     frames = [W.bulb_1080p(10 + k) for k in range(8)]
-    fouts = [api.alloc_image(f) for f in frames]
-    fc = count_frame(api, torch, frames)
-    step = Renderer(api, F, frames, fouts, "batch", api.current_stream())
-    for _ in range(args.warmup):
-        step()
-    times, total, _ = time_steps(torch, step, max(3, args.steps // 4), tstream, flush)
-    n = max(3, args.steps // 4)
-    out["eight_frames_in_flight"] = {"path": "batch", "batch_kernel": F.fr_get_tuning().batch_kernel,
-                                     "ms_per_8_frames": total / n * 1e3,
-                                     "value": (fc[0] + fc[1] + fc[6]) * n / total / 1e6, "unit": "Mrays/s"}
+    mm = measure(args, torch, api, F, frames, "batch", env, n, w, tune=False, compare=False)
+    out["eight_frames_in_flight"] = dict(summary_of(mm, n, peak, peak_derived), path="batch",
+                                         batch_kernel=F.fr_get_tuning().batch_kernel,
+                                         workload="Mandelbulb n=8 1920x1080, frames 10..17 of the camera "
+                                                  "orbit in one fr_render_batch call",
+                                         ms_per_frame=mm["main"]["total_s"] / n * 1e3 / 8)
+    return out
+
+
+def other_configs(args, torch, api, F, env, peak, peak_derived):
+    """The other configurations, each measured in the same run as the headline:
+    the 64-request mixed batch (autotuned schedule against one plain launch per
+    request), the differentiable Julia render (grad/s against finite
+    differences) and one 4K frame of the stress animation (4 jittered samples)."""
+    out = {}
+    keep = F.fr_get_tuning()
+    keep = F.fr_tuning(*[getattr(keep, k) for k, _ in F.fr_tuning._fields_])
+    try:
+        sc, desc = workload("batch_mixed")
+        mm = measure(args, torch, api, F, sc, "batch", env, 5, 3, tune=True, tune_reps=3, compare=True)
+        out["batch_mixed"] = dict(summary_of(mm, 5, peak, peak_derived), workload=desc, path="batch")
+        F.check(F.fr_set_tuning(keep))
+        sc, desc = workload("stress_bulb_4k")
+        mm = measure(args, torch, api, F, sc, "plain", env, 5, 3, tune=True, tune_reps=3, compare=False)
+        out["stress_bulb_4k"] = dict(summary_of(mm, 5, peak, peak_derived), workload=desc, path="plain")
+        F.check(F.fr_set_tuning(keep))
+        sc, desc = workload("diff_julia")
+        g = measure_gradient(args, torch, api, F, sc[0], 20, 5)
+        out["diff_julia"] = dict(g, workload=desc)
+    finally:
+        F.fr_set_tuning(keep)
     return out
 
 

@@ -343,6 +343,17 @@ FR_API fr_status fr_render_backward_ws(const fr_julia_params *params, const fr_p
                                        const float *saved, const float *d_rgba, const float *d_depth,
                                        float *grad, void *workspace, size_t ws_bytes, void *stream);
 
+/* Diagnostic, with no counterpart in the paper: the FP32 fused multiply-add
+ * rate of this GPU, the denominator of the renderer's FP32 roofline.  Launches
+ * `blocks` x `threads` threads (threads 32..256, a multiple of 32), each running
+ * 8 independent chains of iters * 16 fused multiply-adds, and writes one float
+ * per thread to `sink` (device, blocks * threads floats, 4-byte aligned) so
+ * that no chain is dead code.  Time it with events on `stream`;
+ * fr_ffma_probe_flops gives the FP32 operations of one launch (2 per FFMA; 0
+ * for non-positive arguments).  Errors: FR_EINVAL, FR_ECUDA. */
+FR_API fr_status fr_ffma_probe(int32_t blocks, int32_t threads, int32_t iters, float *sink, void *stream);
+FR_API double fr_ffma_probe_flops(int32_t blocks, int32_t threads, int32_t iters);
+
 /* Read / replace the process-wide launch shapes (checked; FR_EINVAL if out of range). */
 FR_API fr_status fr_get_tuning(fr_tuning *out);
 FR_API fr_status fr_set_tuning(const fr_tuning *t);

@@ -96,6 +96,8 @@ SIGNATURES = {
                                         ctypes.POINTER(fr_camera), ctypes.POINTER(fr_light), c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                         c_void_p]),
+    "fr_ffma_probe": (c_int32, [c_int32, c_int32, c_int32, c_void_p, c_void_p]),
+    "fr_ffma_probe_flops": (ctypes.c_double, [c_int32, c_int32, c_int32]),
     "fr_get_tuning": (c_int32, [ctypes.POINTER(fr_tuning)]),
     "fr_set_tuning": (c_int32, [ctypes.POINTER(fr_tuning)]),
     "fr_last_error": (ctypes.c_char_p, []),
@@ -187,6 +189,14 @@ def fr_render_backward_mandelbulb(params, plane, camera, light, saved, d_rgba, d
     return load().fr_render_backward_mandelbulb(ctypes.byref(params), ctypes.byref(plane) if plane else None,
                                                 ctypes.byref(camera), ctypes.byref(light), saved, d_rgba,
                                                 d_depth, grad, workspace, int(ws_bytes), stream)
+
+
+def fr_ffma_probe(blocks, threads, iters, sink, stream=None):
+    return load().fr_ffma_probe(int(blocks), int(threads), int(iters), sink, stream)
+
+
+def fr_ffma_probe_flops(blocks, threads, iters) -> float:
+    return float(load().fr_ffma_probe_flops(int(blocks), int(threads), int(iters)))
 
 
 def fr_get_tuning():
