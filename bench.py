@@ -399,6 +399,8 @@ def measure(args, torch, api, F, scenes, path, env, steps, warmup, clk_index=Non
             del space["batch_kernel"]
         if args.tile_order is not None:
             del space["tile_order"]
+        if args.sample_lanes is not None:
+            del space["sample_lanes"]
         r = autotune.tune(scenes, reps=tune_reps, space=space)  # untimed search over the launch shape
         tuning = {"config": r["config"], "search_ms": r["ms"], "trials": len(r["trials"])}
     elif tune and path == "plain" and len(scenes) == 1:
@@ -409,6 +411,8 @@ def measure(args, torch, api, F, scenes, path, env, steps, warmup, clk_index=Non
             del space["tile_order"]
         if args.single_kernel is not None:
             del space["single_kernel"]
+        if args.sample_lanes is not None:
+            del space["sample_lanes"]
         r = autotune.tune_single(scenes[0], reps=max(tune_reps, 3), space=space, start_kernel=args.single_kernel)
         tuning = {"config": r["config"], "search_ms": r["ms"], "trials": len(r["trials"]),
                   "trial_ms": [[{k: t[k] for k in space}, round(t["ms"], 4)] for t in r["trials"]]}
@@ -585,6 +589,9 @@ def main():
     ap.add_argument("--batch-kernel", type=int, choices=[0, 1], default=None,
                     help="fix fr_render_batch's schedule (1 one-ray-per-thread kernel over all "
                          "tiles, 0 persistent kernel); the autotuner then keeps it")
+    ap.add_argument("--sample-lanes", type=int, choices=[0, 1], default=None,
+                    help="fix where a pixel's 2, 4 or 8 samples run (1 adjacent lanes, 0 in turn on "
+                         "one lane); the autotuner then keeps it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -612,8 +619,11 @@ def main():
 
     B.build()
     F.load()
-    if args.batch_kernel is not None or args.tile_order is not None or args.single_kernel is not None:
+    if (args.batch_kernel is not None or args.tile_order is not None or args.single_kernel is not None
+            or args.sample_lanes is not None):
         t = F.fr_get_tuning()
+        if args.sample_lanes is not None:
+            t.sample_lanes = args.sample_lanes
         if args.batch_kernel is not None:
             t.batch_kernel = args.batch_kernel
         if args.single_kernel is not None:

@@ -222,6 +222,12 @@ typedef struct {
                                     bottom to top.  The hardware starts CTAs roughly in
                                     index order, so this decides which part of the frame
                                     runs first; images are the same bit for bit.      */
+    int32_t sample_lanes;        /* one-ray-per-thread kernels with spp 2, 4 or 8: 1 (default)
+                                    the pixel's samples on spp adjacent lanes (a warp
+                                    covers 4 x 8 / spp pixels, whose jittered rays take
+                                    nearly the same marches), 0 each lane runs its
+                                    pixel's samples in turn (4 x 8 pixels per warp).
+                                    Same images bit for bit.                           */
 } fr_tuning;
 
 /* Render one quaternion Julia image with the one-ray-per-thread kernel

@@ -69,7 +69,7 @@ class fr_tuning(ctypes.Structure):
     _fields_ = [("plain_block", c_int32), ("plain_unroll", c_int32), ("persist_block", c_int32),
                 ("persist_ctas_per_sm", c_int32), ("refill_threshold", c_int32),
                 ("persist_unroll", c_int32), ("single_kernel", c_int32), ("batch_kernel", c_int32),
-                ("tile_order", c_int32)]
+                ("tile_order", c_int32), ("sample_lanes", c_int32)]
 
 
 # every entry point of include/fr.h with its ctypes signature

@@ -4,12 +4,14 @@ For fr_render_batch (tune):
   batch_kernel       1 one-ray-per-thread kernel over all tiles, 0 persistent kernel
   plain_block        threads per CTA of the one-ray-per-thread batch kernel
   tile_order         order of the tiles in the launch (rows, columns, rows upward)
+  sample_lanes       requests with 2, 4 or 8 samples: their samples on adjacent lanes (1) or
+                     in turn on one lane (0)
   persist_block      threads per CTA of the persistent kernel (64, 128, 256)
   refill_threshold   idle lanes that trigger a warp refill (the compaction interval)
   persist_unroll     Julia orbit steps per scheduling round (the unroll depth)
 For one request through fr_render_julia / fr_render_mandelbulb (tune_single):
   single_kernel      0 the single-request kernel, 2 the batch kernel's code
-  plain_block, plain_unroll (orbit-loop unroll depth) and tile_order.
+  plain_block, plain_unroll (orbit-loop unroll depth), tile_order and sample_lanes.
 The search is coordinate descent from the current setting: each knob in turn is
 swept with the others fixed, each candidate timed with CUDA events (median of a
 few calls on the caller's scenes), and a candidate replaces the current
@@ -33,6 +35,7 @@ SPACE = {
     "batch_kernel": (1, 0),
     "plain_block": (32, 64, 128, 256),
     "tile_order": (0, 1, 2),
+    "sample_lanes": (1, 0),
     "persist_block": (64, 128, 256),
     "refill_threshold": (1, 2, 4, 8, 16),
     "persist_unroll": (2, 4, 8),
@@ -42,6 +45,7 @@ SINGLE_SPACE = {
     "plain_block": (32, 64, 128, 256),
     "plain_unroll": (1, 2, 4),
     "tile_order": (0, 1, 2),
+    "sample_lanes": (1, 0),
 }
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 
@@ -97,7 +101,7 @@ def _in_use(knob: str, cfg: dict) -> bool:
     """Whether `knob` changes what fr_render_batch launches under `cfg`."""
     if knob in PERSIST_KNOBS:
         return cfg.get("batch_kernel", 0) == 0
-    if knob in ("plain_block", "tile_order"):
+    if knob in ("plain_block", "tile_order", "sample_lanes"):
         return cfg.get("batch_kernel", 0) == 1
     return True
 
@@ -109,7 +113,14 @@ def tune(scenes, reps: int = 5, passes: int = 1, space: dict | None = None, log=
     configuration applied."""
     outs = [api.alloc_image(s) for s in scenes]
     ws = api.workspace(len(scenes))
-    return _descent(lambda: _time_batch(scenes, outs, ws, reps), space or SPACE, _in_use, passes, log, margin)
+    lanes = _sample_lanes_matter(scenes)
+    return _descent(lambda: _time_batch(scenes, outs, ws, reps), space or SPACE,
+                    lambda k, c: _in_use(k, c) and (k != "sample_lanes" or lanes), passes, log, margin)
+
+
+def _sample_lanes_matter(scenes) -> bool:
+    """sample_lanes changes the launch only for requests with 2, 4 or 8 samples."""
+    return any(s["camera"]["spp"] in (2, 4, 8) for s in scenes)
 
 
 def tune_single(scene, reps: int = 9, passes: int = 1, space: dict | None = None, log=None,
@@ -120,7 +131,9 @@ def tune_single(scene, reps: int = 9, passes: int = 1, space: dict | None = None
     candidate."""
     out = api.alloc_image(scene)
     apply({"single_kernel": 0 if start_kernel is None else start_kernel})
-    return _descent(lambda: _time_single(scene, out, reps), space or SINGLE_SPACE, lambda k, c: True, passes,
+    lanes = _sample_lanes_matter([scene])
+    return _descent(lambda: _time_single(scene, out, reps), space or SINGLE_SPACE,
+                    lambda k, c: k != "sample_lanes" or (lanes and c.get("single_kernel", 0) != 1), passes,
                     log, margin)
 
 

@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 1, 0};
+fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 1, 0, 1};
 
 fr_tuning tuning()
 {
@@ -163,6 +163,7 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
     const long long tiles_y = (cam->height + fr::kTileH - 1) / fr::kTileH;
     R.n_units = (long long)R.tiles_x * tiles_y * 32;
     R.unit_begin = 0;
+    R.spl = 1;
 
     if (!finite_n(li->dir, 3) || !finite_n(li->albedo, 3) || !finite_n(li->background, 4) ||
         !std::isfinite(li->k_ambient) || !std::isfinite(li->k_diffuse))
@@ -218,6 +219,13 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
     return FR_OK;
 }
 
+// lanes per pixel of the one-ray-per-thread kernels: the pixel's samples on
+// adjacent lanes when the tuning asks for it and spp is 2, 4 or 8
+int lanes_per_pixel(const fr_tuning &tu, const fr::DevReq &R)
+{
+    return (tu.sample_lanes && (R.spp == 2 || R.spp == 4 || R.spp == 8)) ? R.spp : 1;
+}
+
 fr_status launched(cudaError_t e)
 {
     if (e != cudaSuccess) return fail(FR_ECUDA, "CUDA launch failed: %s", cudaGetErrorString(e));
@@ -264,7 +272,7 @@ fr_status resolve_requests(const fr_request *reqs, int n_reqs, std::vector<DevRe
 
 extern "C" {
 
-FR_API int32_t fr_abi_version(void) { return 2; }
+FR_API int32_t fr_abi_version(void) { return 3; }
 
 FR_API const char *fr_last_error(void) { return g_err.c_str(); }
 
@@ -291,6 +299,7 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
     if (t->single_kernel < 0 || t->single_kernel > 2) return fail(FR_EINVAL, "single_kernel must be 0, 1 or 2");
     if (t->batch_kernel != 0 && t->batch_kernel != 1) return fail(FR_EINVAL, "batch_kernel must be 0 or 1");
     if (t->tile_order < 0 || t->tile_order > 2) return fail(FR_EINVAL, "tile_order must be 0, 1 or 2");
+    if (t->sample_lanes != 0 && t->sample_lanes != 1) return fail(FR_EINVAL, "sample_lanes must be 0 or 1");
     std::lock_guard<std::mutex> lk(g_tuning_mu);
     g_tuning = *t;
     return FR_OK;
@@ -312,13 +321,15 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
                                          (cudaStream_t)stream));
     }
     if (tu.single_kernel == 2) {
-        // sides of at most 65535 make at most 1.4e8 tiles: the grid stays below the CTA limit
+        // width * height * spp < 2^31 keeps a request below 2^26 tiles in either
+        // layout (32 lanes per tile): the grid stays below the 2^31 - 1 CTA limit
         static thread_local fr::BatchArgs A;
         const long long warps_per_cta = tu.plain_block / 32;
-        const long long ctas = (R.n_units / 32 + warps_per_cta - 1) / warps_per_cta;
         A.reqs[0] = R;
         A.reqs[0].unit_begin = 0;
         A.reqs[0].tile_order = tu.tile_order;
+        A.reqs[0].spl = lanes_per_pixel(tu, R);
+        const long long ctas = (fr::plain_tiles(A.reqs[0]) + warps_per_cta - 1) / warps_per_cta;
         A.n_reqs = 1;
         A.total_units = ctas;
         A.refill_threshold = 1;
@@ -328,6 +339,7 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
     }
     fr::DevReq Q = R;
     Q.tile_order = tu.tile_order;
+    Q.spl = lanes_per_pixel(tu, R);
     return launched(fr::launch_plain(Q, tu.plain_block, tu.plain_unroll, count, (cudaStream_t)stream));
 }
 
@@ -380,6 +392,7 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         if (st != FR_OK) return st;
     }
     const fr_tuning tu = tuning();
+    for (fr::DevReq &R : all) R.spl = tu.batch_kernel == 1 ? lanes_per_pixel(tu, R) : 1;
 
     // costliest requests first: the cheap ones then fill in behind the costly
     // ones' slow pixels at the end of the launch (outputs travel with their
@@ -396,7 +409,7 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     const long long warps_per_cta = tu.plain_block / 32;
-    auto ctas_of = [&](const fr::DevReq &R) { return (R.n_units / 32 + warps_per_cta - 1) / warps_per_cta; };
+    auto ctas_of = [&](const fr::DevReq &R) { return (fr::plain_tiles(R) + warps_per_cta - 1) / warps_per_cta; };
     if (tu.batch_kernel == 1)  // the grid of each launch must fit the 2^31 - 1 CTA limit
         for (int first = 0; first < n_reqs; first += fr::kMaxReqPerLaunch) {
             long long ctas = 0;

@@ -78,6 +78,8 @@ struct __align__(16) DevReq {
     int shading;              // 0 Lambert, 1 Phong + reflection bounce
     int quad_store;           // rgba8 / depth rows may be written 4 pixels per 16-byte store
     int tile_order;           // order of the tiles over the grid (fr_tuning.tile_order)
+    int spl;                  // one-ray-per-thread kernels: lanes per pixel (1, or spp when the
+                              // pixel's samples run on adjacent lanes; fr_tuning.sample_lanes)
     float4 bg;
     uint32_t *rgba8;
     float4 *rgba;
@@ -88,6 +90,13 @@ struct __align__(16) DevReq {
     long long unit_begin; // first queue unit of this request inside a batch
     long long n_units;    // tiles * 32
 };
+
+// warps (tiles of 4 x 8 / spl pixels) one request takes in the one-ray-per-thread kernels
+__host__ __device__ __forceinline__ long long plain_tiles(const DevReq &R)
+{
+    const int th = kTileH / R.spl;
+    return (long long)R.tiles_x * ((R.height + th - 1) / th);
+}
 
 // ------------------------------------------------------------------ arithmetic
 // Every rounding step below is spelled out (fmaf = one fused multiply-add,
@@ -797,26 +806,32 @@ __device__ __forceinline__ void store_pixel_extras(const DevReq &R, long long id
     if (R.trap) R.trap[idx] = (flags & kFlagHit) ? orbit_trap(R, xhit) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
-// Packed colour and depth of a warp's 4 x 8 tile, called by all 32 lanes
-// together (valid: the lane's pixel lies inside the image).  The 4 lanes of a
-// tile row hold 4 adjacent pixels: where the row is complete and the image
-// width and both buffers allow 16-byte alignment (quad_store), the row's
-// first lane gathers them by shuffles and writes one 16-byte store per
-// buffer; otherwise every valid lane writes its own 4 bytes.
+// Packed colour and depth of a warp's tile, called by all 32 lanes together
+// (valid: the lane holds a finished pixel inside the image).  Pixel q of the
+// tile sits on lane q * spl (spl lanes per pixel), and the tile is 4 pixels
+// wide, so the 4 adjacent pixels of a tile row are on lanes spl apart: where
+// the row is complete and the image width and both buffers allow 16-byte
+// alignment (quad_store), the row's first pixel lane gathers them by shuffles
+// and writes one 16-byte store per buffer; otherwise every valid lane writes
+// its own 4 bytes.
 __device__ __forceinline__ void store_rgba8_depth(const DevReq &R, int px, int py, bool valid, uint32_t c8,
-                                                  float d)
+                                                  float d, int spl = 1)
 {
     static_assert(kTileW == 4, "a tile row is one 16-byte quad");
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const uint32_t c1 = __shfl_down_sync(full, c8, 1), c2 = __shfl_down_sync(full, c8, 2),
-                   c3 = __shfl_down_sync(full, c8, 3);
-    const float d1 = __shfl_down_sync(full, d, 1), d2 = __shfl_down_sync(full, d, 2),
-                d3 = __shfl_down_sync(full, d, 3);
-    const unsigned row = (__ballot_sync(full, valid) >> (lane & ~3)) & 0xfu;
+    const uint32_t c1 = __shfl_down_sync(full, c8, spl), c2 = __shfl_down_sync(full, c8, 2 * spl),
+                   c3 = __shfl_down_sync(full, c8, 3 * spl);
+    const float d1 = __shfl_down_sync(full, d, spl), d2 = __shfl_down_sync(full, d, 2 * spl),
+                d3 = __shfl_down_sync(full, d, 3 * spl);
+    const int first = lane & ~(4 * spl - 1);  // the row's first pixel lane
+    const unsigned ok = __ballot_sync(full, valid);
+    const unsigned want = (1u << first) | (1u << (first + spl)) | (1u << (first + 2 * spl)) |
+                          (1u << (first + 3 * spl));
+    const bool row = (ok & want) == want;
     const long long idx = (long long)py * R.width + px;
-    if (R.quad_store && row == 0xfu) {
-        if ((lane & 3) == 0) {
+    if (R.quad_store && row) {
+        if (lane == first) {
             if (R.rgba8) *reinterpret_cast<uint4 *>(R.rgba8 + idx) = make_uint4(c8, c1, c2, c3);
             if (R.depth) *reinterpret_cast<float4 *>(R.depth + idx) = make_float4(d, d1, d2, d3);
         }

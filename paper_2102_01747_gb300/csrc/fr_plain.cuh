@@ -12,15 +12,20 @@
 
 namespace fr {
 
-// Pixel of `lane` in tile number `tile` of request R.  Tiles are numbered in
-// launch order (the hardware hands CTAs to SMs roughly in index order), laid
-// over the image by R.tile_order: 0 rows of tiles top to bottom, 1 columns of
-// tiles left to right, 2 rows bottom to top.  The grid is padded to whole
-// CTAs; the padding tiles land past the image's right or bottom edge in every
-// order, so their lanes fail the px < width, py < height test.
-__device__ __forceinline__ void tile_pixel(const DevReq &R, long long tile, int lane, int &px, int &py)
+// Pixel and first sample of `lane` in tile number `tile` of request R.  A
+// tile is 4 pixels wide and 8 / R.spl tall, pixel q of the tile (row-major)
+// on lanes q * spl .. q * spl + spl - 1, sample k on the k-th of them.  Tiles
+// are numbered in launch order (the hardware hands CTAs to SMs roughly in
+// index order), laid over the image by R.tile_order: 0 rows of tiles top to
+// bottom, 1 columns of tiles left to right, 2 rows bottom to top.  The grid is
+// padded to whole CTAs; the padding tiles land past the image's right or
+// bottom edge in every order, so their lanes fail the px < width, py < height
+// test.
+__device__ __forceinline__ void tile_pixel(const DevReq &R, long long tile, int lane, int &px, int &py,
+                                           int &sample)
 {
-    const long long tiles_y = (R.height + kTileH - 1) / kTileH;
+    const int th = kTileH / R.spl;
+    const long long tiles_y = (R.height + th - 1) / th;
     long long tx, ty;
     if (R.tile_order == 1) {
         tx = tile / tiles_y;
@@ -30,9 +35,12 @@ __device__ __forceinline__ void tile_pixel(const DevReq &R, long long tile, int 
         ty = tile / R.tiles_x;
         if (R.tile_order == 2 && ty < tiles_y) ty = tiles_y - 1 - ty;
     }
-    px = (int)tx * kTileW + (lane & (kTileW - 1));
-    py = (int)ty * kTileH + (lane / kTileW);
+    const int q = lane / R.spl;
+    sample = lane - q * R.spl;
+    px = (int)tx * kTileW + (q & (kTileW - 1));
+    py = (int)ty * th + (q / kTileW);
 }
+
 
 // BAN: compiled with the Mandelbulb's analytic normal (normal_at)
 template <int KIND, int U, bool COUNT, bool PHONG, bool BAN>
@@ -41,24 +49,23 @@ __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevR
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long tile = gtid >> 5;
     const int lane = threadIdx.x & 31;
-    int px, py;
-    tile_pixel(R, tile, lane, px, py);
+    int px, py, sample;
+    tile_pixel(R, tile, lane, px, py, sample);
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
     const bool valid = px < R.width && py < R.height;
     uint32_t c8 = 0;
     float depth = 0.0f;
-    if (valid) render_pixel<KIND, U, COUNT, PHONG, BAN>(R, px, py, cnt, c8, depth);
-    store_rgba8_depth(R, px, py, valid, c8, depth);
+    render_pixel<KIND, U, COUNT, PHONG, BAN>(R, px, py, sample, valid, cnt, c8, depth);
+    store_rgba8_depth(R, px, py, valid && sample == 0, c8, depth, R.spl);
     if (COUNT) flush_counters(cnt, R.stats);
 }
 
 template <int KIND, int U, bool COUNT, bool PHONG = false, bool BAN = false>
 static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 {
-    const long long tiles_y = (R.height + kTileH - 1) / kTileH;
-    const long long threads = (long long)R.tiles_x * tiles_y * 32;
+    const long long threads = plain_tiles(R) * 32;
     const long long grid = (threads + block - 1) / block;
     plain_kernel<KIND, U, COUNT, PHONG, BAN><<<(unsigned)grid, block, 0, s>>>(R);
     return cudaGetLastError();
@@ -92,21 +99,19 @@ __global__ void __maxnreg__(72) batch_plain_kernel(const __grid_constant__ Batch
     const DevReq &R = A.reqs[lo];
     const long long tile = (cta - R.unit_begin) * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    int px, py;
-    tile_pixel(R, tile, lane, px, py);
+    int px, py, sample;
+    tile_pixel(R, tile, lane, px, py, sample);
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
     const bool valid = px < R.width && py < R.height;
     uint32_t c8 = 0;
     float depth = 0.0f;
-    if (valid) {
-        if (R.kind == 0)
-            render_pixel<0, U, COUNT, PHONG, true>(R, px, py, cnt, c8, depth);
-        else
-            render_pixel<1, U, COUNT, PHONG, true>(R, px, py, cnt, c8, depth);
-    }
-    store_rgba8_depth(R, px, py, valid, c8, depth);
+    if (R.kind == 0)
+        render_pixel<0, U, COUNT, PHONG, true>(R, px, py, sample, valid, cnt, c8, depth);
+    else
+        render_pixel<1, U, COUNT, PHONG, true>(R, px, py, sample, valid, cnt, c8, depth);
+    store_rgba8_depth(R, px, py, valid && sample == 0, c8, depth, R.spl);
     if (COUNT && R.stats) flush_counters(cnt, R.stats);
 }
 

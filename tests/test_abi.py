@@ -41,7 +41,7 @@ def test_exports_every_declared_symbol(F):
     for n in names:
         assert hasattr(lib, n), n
         assert n in F.SIGNATURES, "binding lacks " + n
-    assert F.fr_abi_version() == 2
+    assert F.fr_abi_version() == 3
 
 
 def test_struct_layout_matches_header(F):
