@@ -164,6 +164,7 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
     R.n_units = (long long)R.tiles_x * tiles_y * 32;
     R.unit_begin = 0;
     R.spl = 1;
+    R.spl_log2 = 0;
 
     if (!finite_n(li->dir, 3) || !finite_n(li->albedo, 3) || !finite_n(li->background, 4) ||
         !std::isfinite(li->k_ambient) || !std::isfinite(li->k_diffuse))
@@ -224,6 +225,12 @@ fr_status resolve_common(fr::DevReq &R, const fr_plane *pl, const fr_camera *cam
 int lanes_per_pixel(const fr_tuning &tu, const fr::DevReq &R)
 {
     return (tu.sample_lanes && (R.spp == 2 || R.spp == 4 || R.spp == 8)) ? R.spp : 1;
+}
+
+void set_lanes(fr::DevReq &R, int spl)
+{
+    R.spl = spl;
+    R.spl_log2 = spl == 8 ? 3 : spl == 4 ? 2 : spl == 2 ? 1 : 0;
 }
 
 fr_status launched(cudaError_t e)
@@ -328,7 +335,7 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
         A.reqs[0] = R;
         A.reqs[0].unit_begin = 0;
         A.reqs[0].tile_order = tu.tile_order;
-        A.reqs[0].spl = lanes_per_pixel(tu, R);
+        set_lanes(A.reqs[0], lanes_per_pixel(tu, R));
         const long long ctas = (fr::plain_tiles(A.reqs[0]) + warps_per_cta - 1) / warps_per_cta;
         A.n_reqs = 1;
         A.total_units = ctas;
@@ -339,7 +346,7 @@ static fr_status launch_single(const fr::DevReq &R, bool count, void *stream)
     }
     fr::DevReq Q = R;
     Q.tile_order = tu.tile_order;
-    Q.spl = lanes_per_pixel(tu, R);
+    set_lanes(Q, lanes_per_pixel(tu, R));
     return launched(fr::launch_plain(Q, tu.plain_block, tu.plain_unroll, count, (cudaStream_t)stream));
 }
 
@@ -392,7 +399,7 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         if (st != FR_OK) return st;
     }
     const fr_tuning tu = tuning();
-    for (fr::DevReq &R : all) R.spl = tu.batch_kernel == 1 ? lanes_per_pixel(tu, R) : 1;
+    for (fr::DevReq &R : all) set_lanes(R, tu.batch_kernel == 1 ? lanes_per_pixel(tu, R) : 1);
 
     // costliest requests first: the cheap ones then fill in behind the costly
     // ones' slow pixels at the end of the launch (outputs travel with their

@@ -80,6 +80,7 @@ struct __align__(16) DevReq {
     int tile_order;           // order of the tiles over the grid (fr_tuning.tile_order)
     int spl;                  // one-ray-per-thread kernels: lanes per pixel (1, or spp when the
                               // pixel's samples run on adjacent lanes; fr_tuning.sample_lanes)
+    int spl_log2;             // log2(spl)
     float4 bg;
     uint32_t *rgba8;
     float4 *rgba;

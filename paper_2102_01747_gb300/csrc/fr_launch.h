@@ -49,6 +49,12 @@ cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, in
 // the single-request kernel compiled with the Mandelbulb's analytic normal (unroll 1)
 cudaError_t launch_plain_ban(const DevReq &R, int block, bool count, cudaStream_t s);
 
+// the one-ray-per-thread kernels with a pixel's samples on R.spl adjacent lanes
+// (unroll 1): one request, or a batch launch in which some request has spl > 1
+cudaError_t launch_plain_lanes(const DevReq &R, int block, bool count, cudaStream_t s);
+cudaError_t launch_batch_plain_lanes(const BatchArgs &A, long long ctas, int block, bool count, bool phong,
+                                     cudaStream_t s);
+
 // lane-state-machine forward kernel without the queue: one pixel per lane, all tiles launched
 cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, bool phong, cudaStream_t s);
 

@@ -10,6 +10,8 @@ namespace fr {
 cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, int unroll, bool count,
                                bool phong, cudaStream_t s)
 {
+    for (int i = 0; i < A.n_reqs; i++)
+        if (A.reqs[i].spl > 1) return launch_batch_plain_lanes(A, ctas, block, count, phong, s);
     if (phong) return count ? launch_batch_plain_t<1, true, true>(A, ctas, block, s)
                             : launch_batch_plain_t<1, false, true>(A, ctas, block, s);
     if (count) return launch_batch_plain_t<1, true, false>(A, ctas, block, s);
@@ -20,6 +22,7 @@ cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, in
 // Phong requests run the Phong-capable instantiation at unroll 1
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s)
 {
+    if (R.spl > 1) return launch_plain_lanes(R, block, count, s);
     if (R.kind == 1 && R.normal_mode == 2) return launch_plain_ban(R, block, count, s);
     if (R.shading) {
         if (R.kind == 0)

@@ -21,53 +21,73 @@ namespace fr {
 // padded to whole CTAs; the padding tiles land past the image's right or
 // bottom edge in every order, so their lanes fail the px < width, py < height
 // test.
+// spl is 1, 2, 4 or 8 (R.spl_log2 its log2) and width * height * spp < 2^31
+// keeps a request below 2^26 tiles, so the arithmetic is 32-bit shifts and
+// divisions.
+template <bool LANES>
 __device__ __forceinline__ void tile_pixel(const DevReq &R, long long tile, int lane, int &px, int &py,
                                            int &sample)
 {
-    const int th = kTileH / R.spl;
-    const long long tiles_y = (R.height + th - 1) / th;
-    long long tx, ty;
+    const unsigned t = (unsigned)tile;
+    const int spl_log2 = LANES ? R.spl_log2 : 0;
+    const int th_log2 = 3 - spl_log2;  // tile height 8 / spl = 2^th_log2
+    const unsigned tiles_y = ((unsigned)R.height + (1u << th_log2) - 1u) >> th_log2;
+    unsigned tx, ty;
     if (R.tile_order == 1) {
-        tx = tile / tiles_y;
-        ty = tile % tiles_y;
+        tx = t / tiles_y;
+        ty = t - tx * tiles_y;
     } else {
-        tx = tile % R.tiles_x;
-        ty = tile / R.tiles_x;
-        if (R.tile_order == 2 && ty < tiles_y) ty = tiles_y - 1 - ty;
+        ty = t / (unsigned)R.tiles_x;
+        tx = t - ty * (unsigned)R.tiles_x;
+        if (R.tile_order == 2 && ty < tiles_y) ty = tiles_y - 1u - ty;
     }
-    const int q = lane / R.spl;
-    sample = lane - q * R.spl;
+    const int q = lane >> spl_log2;
+    sample = lane & ((1 << spl_log2) - 1);
     px = (int)tx * kTileW + (q & (kTileW - 1));
-    py = (int)ty * th + (q / kTileW);
+    py = ((int)ty << th_log2) + (q / kTileW);
 }
 
 
-// BAN: compiled with the Mandelbulb's analytic normal (normal_at)
-template <int KIND, int U, bool COUNT, bool PHONG, bool BAN>
-__global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevReq R)
+// One pixel of a lane (LANES false: each lane's pixel, all its samples in
+// turn; LANES true: the samples of a pixel on R.spl adjacent lanes), called by
+// all 32 lanes of the warp; the packed colour and depth of finished pixels go
+// to the warp's quad store.
+template <int KIND, int U, bool COUNT, bool PHONG, bool BAN, bool LANES>
+__device__ __forceinline__ void shade_tile(const DevReq &R, long long tile, Counters &cnt)
 {
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tile = gtid >> 5;
     const int lane = threadIdx.x & 31;
     int px, py, sample;
-    tile_pixel(R, tile, lane, px, py, sample);
-    Counters cnt;
-    if (COUNT)
-        for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
+    tile_pixel<LANES>(R, tile, lane, px, py, sample);
     const bool valid = px < R.width && py < R.height;
     uint32_t c8 = 0;
     float depth = 0.0f;
-    render_pixel<KIND, U, COUNT, PHONG, BAN>(R, px, py, sample, valid, cnt, c8, depth);
-    store_rgba8_depth(R, px, py, valid && sample == 0, c8, depth, R.spl);
+    if constexpr (LANES) {
+        render_pixel_lanes<KIND, U, COUNT, PHONG, BAN>(R, px, py, sample, valid, cnt, c8, depth);
+        store_rgba8_depth(R, px, py, valid && sample == 0, c8, depth, R.spl);
+    } else {
+        if (valid) render_pixel<KIND, U, COUNT, PHONG, BAN>(R, px, py, cnt, c8, depth);
+        store_rgba8_depth(R, px, py, valid, c8, depth);
+    }
+}
+
+// BAN: compiled with the Mandelbulb's analytic normal (normal_at)
+template <int KIND, int U, bool COUNT, bool PHONG, bool BAN, bool LANES = false>
+__global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevReq R)
+{
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    Counters cnt;
+    if (COUNT)
+        for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
+    shade_tile<KIND, U, COUNT, PHONG, BAN, LANES>(R, gtid >> 5, cnt);
     if (COUNT) flush_counters(cnt, R.stats);
 }
 
-template <int KIND, int U, bool COUNT, bool PHONG = false, bool BAN = false>
+template <int KIND, int U, bool COUNT, bool PHONG = false, bool BAN = false, bool LANES = false>
 static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 {
     const long long threads = plain_tiles(R) * 32;
     const long long grid = (threads + block - 1) / block;
-    plain_kernel<KIND, U, COUNT, PHONG, BAN><<<(unsigned)grid, block, 0, s>>>(R);
+    plain_kernel<KIND, U, COUNT, PHONG, BAN, LANES><<<(unsigned)grid, block, 0, s>>>(R);
     return cudaGetLastError();
 }
 
@@ -83,7 +103,7 @@ static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 // to itself the compiler takes 80, with which the 64-request mixed batch runs
 // 36.0 ms against 33.3 (64 registers: 33.5).  fr_render_* can also launch it
 // with one request (fr_tuning.single_kernel = 2, autotuned).
-template <int U, bool COUNT, bool PHONG>
+template <int U, bool COUNT, bool PHONG, bool LANES = false>
 __global__ void __maxnreg__(72) batch_plain_kernel(const __grid_constant__ BatchArgs A)
 {
     const int warps = blockDim.x >> 5;
@@ -98,27 +118,20 @@ __global__ void __maxnreg__(72) batch_plain_kernel(const __grid_constant__ Batch
     }
     const DevReq &R = A.reqs[lo];
     const long long tile = (cta - R.unit_begin) * warps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    int px, py, sample;
-    tile_pixel(R, tile, lane, px, py, sample);
     Counters cnt;
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
-    const bool valid = px < R.width && py < R.height;
-    uint32_t c8 = 0;
-    float depth = 0.0f;
     if (R.kind == 0)
-        render_pixel<0, U, COUNT, PHONG, true>(R, px, py, sample, valid, cnt, c8, depth);
+        shade_tile<0, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
     else
-        render_pixel<1, U, COUNT, PHONG, true>(R, px, py, sample, valid, cnt, c8, depth);
-    store_rgba8_depth(R, px, py, valid && sample == 0, c8, depth, R.spl);
+        shade_tile<1, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
     if (COUNT && R.stats) flush_counters(cnt, R.stats);
 }
 
-template <int U, bool COUNT, bool PHONG>
+template <int U, bool COUNT, bool PHONG, bool LANES = false>
 static cudaError_t launch_batch_plain_t(const BatchArgs &A, long long ctas, int block, cudaStream_t s)
 {
-    batch_plain_kernel<U, COUNT, PHONG><<<(unsigned)ctas, block, 0, s>>>(A);
+    batch_plain_kernel<U, COUNT, PHONG, LANES><<<(unsigned)ctas, block, 0, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -207,20 +207,53 @@ __device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro,
 // warp's quad store (store_rgba8_depth).  PHONG compiles the Phong +
 // mirror-ray path in (requests still choose it with R.shading); without it the
 // Lambert-only code keeps fewer registers.
-//
-// Called by all 32 lanes of the warp together.  With R.spl = 1 each lane runs
-// all samples of its pixel in turn.  With R.spl = spp the pixel's samples run
-// on spl adjacent lanes, sample k on the k-th: the 32 rays of a warp then come
-// from 32 / spp neighbouring pixels (a tile 4 x 8 / spp pixels) whose samples
-// are a fraction of a pixel apart, so they take nearly the same march and orbit
-// lengths and keep more lanes busy.  The pixel's first lane then folds in the
-// other lanes' results in sample order -- the same additions in the same order
-// as the loop -- so both layouts give the same bits.  `sample` is the lane's
-// first sample, `valid` whether its pixel lies inside the image; the results
-// are the first lane's.
 template <int KIND, int U, bool COUNT, bool PHONG, bool BAN = false>
-__device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, int sample, bool valid,
-                                             Counters &cnt, uint32_t &c8, float &depth)
+__device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Counters &cnt, uint32_t &c8,
+                                             float &depth)
+{
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float dmin = __int_as_float(0x7f800000);
+    float3 xh = v3(0.0f, 0.0f, 0.0f);
+    uint32_t fl = 0;
+    for (int s = 0; s < R.spp; s++) {
+        float3 ro, rd, x;
+        float t;
+        uint32_t f;
+        camera_ray(R, px, py, s, ro, rd);
+        if (COUNT) cnt.v[kStatPrimaryRays] += 1;
+        float4 c;
+        if constexpr (PHONG)
+            c = trace_sample_phong<KIND, U, COUNT, BAN>(R, ro, rd, t, f, x, cnt);
+        else
+            c = trace_sample<KIND, U, COUNT, BAN>(R, ro, rd, t, f, x, cnt);
+        acc4(acc, c);
+        if ((f & kFlagHit) && t < dmin) {
+            dmin = t;
+            xh = x;
+        }
+        fl |= f;
+    }
+    const float4 mean = mean4(acc, R.spp);
+    store_pixel_extras(R, (long long)py * R.width + px, mean, xh, fl);
+    c8 = pack_rgba8(mean);
+    depth = dmin;
+}
+
+// The same pixel, called by all 32 lanes of the warp together, with its spp
+// samples on R.spl adjacent lanes: sample k on the k-th when R.spl = spp (2, 4
+// or 8), all samples in turn on one lane when R.spl = 1 (requests of a batch
+// launch that some other request's spl > 1 put on this code).  With spl = spp
+// the warp's 32 rays come from 32 / spp neighbouring pixels (a tile
+// 4 x 8 / spp pixels) whose samples are a fraction of a pixel apart, so they
+// take nearly the same march and orbit lengths and keep more lanes busy.  The
+// pixel's first lane folds in the other lanes' results in sample order -- the
+// same additions in the same order as render_pixel's loop -- so both layouts
+// give the same bits; its results are the pixel's.  `valid`: the pixel lies
+// inside the image.  (Kernels of their own: carried in the one-lane kernels,
+// this code cost the 1080p frame 2.5 %.)
+template <int KIND, int U, bool COUNT, bool PHONG, bool BAN = false>
+__device__ __forceinline__ void render_pixel_lanes(const DevReq &R, int px, int py, int sample, bool valid,
+                                                   Counters &cnt, uint32_t &c8, float &depth)
 {
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float dmin = __int_as_float(0x7f800000);
@@ -246,28 +279,32 @@ __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, in
             fl |= f;
         }
     }
-    // samples 1 .. spl - 1 of the pixel, from the next lanes, in sample order;
-    // every lane folds, so the shuffles read each lane's own sample (c0 .. f0),
-    // not its running fold
-    const unsigned full = 0xffffffffu;
-    const int first = (threadIdx.x & 31) & ~(R.spl - 1);
-    const float4 c0 = acc;
-    const float t0 = dmin;
-    const float3 x0 = xh;
-    const uint32_t f0 = fl;
-    for (int j = 1; j < R.spl; j++) {
-        const float4 cj = make_float4(__shfl_sync(full, c0.x, first + j), __shfl_sync(full, c0.y, first + j),
-                                      __shfl_sync(full, c0.z, first + j), __shfl_sync(full, c0.w, first + j));
-        const float tj = __shfl_sync(full, t0, first + j);
-        const float3 xj = v3(__shfl_sync(full, x0.x, first + j), __shfl_sync(full, x0.y, first + j),
-                             __shfl_sync(full, x0.z, first + j));
-        const uint32_t fj = __shfl_sync(full, f0, first + j);
-        acc4(acc, cj);
-        if ((fj & kFlagHit) && tj < dmin) {
-            dmin = tj;
-            xh = xj;
+    if (R.spl > 1) {
+        // the pixel's samples from its lanes, in sample order: every lane folds,
+        // so the shuffles read each lane's own sample (c0 .. f0)
+        const unsigned full = 0xffffffffu;
+        const int first = (threadIdx.x & 31) & ~(R.spl - 1);
+        const float4 c0 = acc;
+        const float t0 = dmin;
+        const float3 x0 = xh;
+        const uint32_t f0 = fl;
+        acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        dmin = __int_as_float(0x7f800000);
+        fl = 0;
+        for (int j = 0; j < R.spl; j++) {
+            const float4 cj = make_float4(__shfl_sync(full, c0.x, first + j), __shfl_sync(full, c0.y, first + j),
+                                          __shfl_sync(full, c0.z, first + j), __shfl_sync(full, c0.w, first + j));
+            const float tj = __shfl_sync(full, t0, first + j);
+            const float3 xj = v3(__shfl_sync(full, x0.x, first + j), __shfl_sync(full, x0.y, first + j),
+                                 __shfl_sync(full, x0.z, first + j));
+            const uint32_t fj = __shfl_sync(full, f0, first + j);
+            acc4(acc, cj);
+            if ((fj & kFlagHit) && tj < dmin) {
+                dmin = tj;
+                xh = xj;
+            }
+            fl |= fj;
         }
-        fl |= fj;
     }
     const float4 mean = mean4(acc, R.spp);
     if (valid && sample == 0) store_pixel_extras(R, (long long)py * R.width + px, mean, xh, fl);
