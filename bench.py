@@ -80,6 +80,10 @@ def workload(name: str, rank: int = 0):
     if name == "bulb_1080p":
         return [W.bulb_1080p(10 + rank)], ("Mandelbulb n=8 1920x1080, 12 iterations, bailout 2, "
                                            "shadow ray, cut z=0.1, frame %d" % (10 + rank))
+    if name == "bulb_1080p_orbit8":
+        return [W.bulb_1080p(10 + 8 * rank + k) for k in range(8)], (
+            "Mandelbulb n=8 1920x1080, 8 consecutive frames of the camera orbit (from frame %d) in one "
+            "fr_render_batch call" % (10 + 8 * rank))
     if name == "bulb_small":
         return [W.bulb_1080p(10 + rank, 480, 270)], "Mandelbulb n=8 480x270 (same scene, small case)"
     if name == "julia_256":
