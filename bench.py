@@ -34,10 +34,14 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
 # divided by the iterations counted on the same scene (Mandelbulb n = 8 at
 # 1920x1080: 8.534 G / 50.88 M = 167.7; Julia p = 2 at 256x256:
-# 364.9 M / 10.27 M = 35.6).  The degree-3 Julia figure is the degree-2 one
-# scaled by the ratio of their orbit-step arithmetic (28 / 24); other
-# Mandelbulb powers take the n = 8 figure (same calls per step).
-FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5, ("bulb", 8): 167.7}
+# 364.9 M / 10.27 M = 35.6; Mandelbulb powers 2..10 at 960x540, the same
+# scene and camera, one request each).  The degree-3 Julia figure is the
+# degree-2 one scaled by the ratio of their orbit-step arithmetic (28 / 24);
+# Mandelbulb powers 11..16 take the n = 10 figure.
+FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5,
+                  ("bulb", 2): 150.1, ("bulb", 3): 154.7, ("bulb", 4): 159.9, ("bulb", 5): 163.7,
+                  ("bulb", 6): 166.8, ("bulb", 7): 166.8, ("bulb", 8): 167.7, ("bulb", 9): 172.0,
+                  ("bulb", 10): 173.9}
 # The algorithmic count of the same work: the operations of the listings'
 # formulas as written, each math-library call (sqrt, pow, acos, atan2, sin,
 # cos, log) counted as one operation, nothing for the library's internals.
@@ -84,6 +88,13 @@ def workload(name: str, rank: int = 0):
         return [W.bulb_1080p(10 + 8 * rank + k) for k in range(8)], (
             "Mandelbulb n=8 1920x1080, 8 consecutive frames of the camera orbit (from frame %d) in one "
             "fr_render_batch call" % (10 + 8 * rank))
+    if name == "bulb_powers":
+        sc = []
+        for n in range(2, 11):
+            s = W.bulb_1080p(10 + rank, 960, 540)
+            s["n"] = n
+            sc.append(s)
+        return sc, "Mandelbulb powers n = 2..10, 960x540 each (bulb_1080p scene), one request per power"
     if name == "bulb_small":
         return [W.bulb_1080p(10 + rank, 480, 270)], "Mandelbulb n=8 480x270 (same scene, small case)"
     if name == "julia_256":
@@ -116,8 +127,8 @@ def workload(name: str, rank: int = 0):
 
 
 def flops_per_iter(scene) -> float:
-    key = (scene["kind"], scene["p"] if scene["kind"] == "julia" else scene["n"])
-    return FLOPS_PER_ITER.get(key, FLOPS_PER_ITER[("bulb", 8)] if scene["kind"] == "bulb" else 35.6)
+    key = (scene["kind"], scene["p"] if scene["kind"] == "julia" else min(scene["n"], 10))
+    return FLOPS_PER_ITER[key]
 
 
 def alg_flops(scene, counts) -> float:
@@ -745,6 +756,8 @@ def main():
         "orbit_iters_per_s": counts[5] * args.steps * world / total_s,
         "per_step": {"rays": rays_per_step, "primary_rays": counts[0], "shadow_rays": counts[1],
                      "mirror_rays": counts[6], "de_calls": des_of(counts), "orbit_iters": counts[5]},
+        "per_request": ([{"rays": rays_of(c), "de_calls": des_of(c), "orbit_iters": c[5]} for c in m["per"]]
+                        if 1 < len(scenes) <= 16 else None),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "Mrays/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": out_bytes, "serial_value": e2e_serial,

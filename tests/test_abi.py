@@ -340,3 +340,25 @@ def test_static_batch_checks_requests_before_any_cuda_call(F):
     arr[0].julia.p = 5
     assert F.fr_render_batch_static(arr, 2, None) == F.FR_EINVAL
     assert "request 0" in F.fr_last_error() and "degree" in F.fr_last_error()
+
+
+def test_ffma_probe_host_checks_and_flop_count(F):
+    """fr_ffma_probe refuses bad launch shapes and a NULL sink on the host;
+    fr_ffma_probe_flops counts 2 flops per FFMA of 8 chains x 16 links per trip."""
+    lib = F.load()
+    assert F.fr_ffma_probe_flops(2, 64, 3) == 2 * 2 * 64 * 3 * 16 * 8
+    assert F.fr_ffma_probe_flops(0, 64, 3) == 0.0
+    assert lib.fr_ffma_probe(0, 256, 10, None, None) == F.FR_EINVAL
+    assert lib.fr_ffma_probe(8, 48, 10, None, None) == F.FR_EINVAL and "threads" in F.fr_last_error()
+    assert lib.fr_ffma_probe(8, 256, 0, None, None) == F.FR_EINVAL
+    assert lib.fr_ffma_probe(8, 256, 10, None, None) == F.FR_EINVAL and "sink" in F.fr_last_error()
+
+
+def test_sample_lanes_tuning_checked(F):
+    t = F.fr_get_tuning()
+    old = tuple(getattr(t, n) for n, _ in F.fr_tuning._fields_)
+    assert t.sample_lanes == 1  # default: a pixel's 2, 4 or 8 samples on adjacent lanes
+    bad = F.fr_tuning(*old)
+    bad.sample_lanes = 2
+    assert F.fr_set_tuning(bad) == F.FR_EINVAL and "sample_lanes" in F.fr_last_error()
+    assert F.fr_set_tuning(F.fr_tuning(*old)) == F.FR_OK
