@@ -39,8 +39,8 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # degree-2 one scaled by the ratio of their orbit-step arithmetic (28 / 24);
 # Mandelbulb powers 11..16 take the n = 10 figure.
 FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5,
-                  ("bulb", 2): 150.1, ("bulb", 3): 154.7, ("bulb", 4): 159.9, ("bulb", 5): 163.7,
-                  ("bulb", 6): 166.8, ("bulb", 7): 166.8, ("bulb", 8): 167.7, ("bulb", 9): 172.0,
+                  ("bulb", 2): 153.1, ("bulb", 3): 157.6, ("bulb", 4): 161.9, ("bulb", 5): 165.6,
+                  ("bulb", 6): 167.8, ("bulb", 7): 168.7, ("bulb", 8): 167.7, ("bulb", 9): 172.9,
                   ("bulb", 10): 173.9}
 # The algorithmic count of the same work: the operations of the listings'
 # formulas as written, each math-library call (sqrt, pow, acos, atan2, sin,

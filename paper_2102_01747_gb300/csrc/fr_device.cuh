@@ -274,15 +274,19 @@ __device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
     o.dz = 1.0f;
 }
 
-// r^k for an integer k >= 0 by binary exponentiation (each product rounded
-// once, so r^7 carries at most 4 roundings)
+// r^k for an integer 0 <= k < 16 by binary exponentiation (each product
+// rounded once, so r^7 carries at most 4 roundings).  Unrolled over the four
+// bits of k with the products selected, not branched on: the same products in
+// the same order as the loop over k's bits (res starts at 1, and 1 * b is b
+// exactly), without its data-dependent branches.
 __device__ __forceinline__ float ipow(float r, int k)
 {
     float res = 1.0f, b = r;
-    while (k > 0) {
-        if (k & 1) res = mul(res, b);
-        k >>= 1;
-        if (k) b = mul(b, b);
+#pragma unroll
+    for (int bit = 0; bit < 4; bit++) {
+        const float p = mul(res, b);
+        res = ((k >> bit) & 1) ? p : res;
+        b = mul(b, b);
     }
     return res;
 }
