@@ -450,7 +450,7 @@ def measure(args, torch, api, F, scenes, path, env, steps, warmup, clk_index=Non
     if path == "plain":  # the kernel fr_render_* launches under the tuned single_kernel
         kern = {0: "plain_kernel", 1: "persist_kernel", 2: "batch_plain_kernel"}[tu.single_kernel]
     else:
-        kern = "batch_plain_kernel" if tu.batch_kernel == 1 else "persist_kernel"
+        kern = {0: "persist_kernel", 1: "batch_plain_kernel", 2: "batch_refill_kernel"}[tu.batch_kernel]
     main_r = results[path]
     return {"per": per, "counts": tot, "flops_ncu": flops_ncu, "flops_alg": flops_alg, "outs": outs,
             "results": results, "main": main_r, "kernel": kern, "tuning": tuning,
@@ -601,9 +601,10 @@ def main():
     ap.add_argument("--tile-order", type=int, choices=(0, 1, 2), default=None,
                     help="fix the tile order of the one-ray-per-thread kernels (0 rows, 1 columns, "
                          "2 rows upward); the autotuner then keeps it")
-    ap.add_argument("--batch-kernel", type=int, choices=[0, 1], default=None,
+    ap.add_argument("--batch-kernel", type=int, choices=[0, 1, 2], default=None,
                     help="fix fr_render_batch's schedule (1 one-ray-per-thread kernel over all "
-                         "tiles, 0 persistent kernel); the autotuner then keeps it")
+                         "tiles, 2 persistent warps taking tiles from a queue, 0 persistent lane "
+                         "state machine); the autotuner then keeps it")
     ap.add_argument("--sample-lanes", type=int, choices=[0, 1], default=None,
                     help="fix where a pixel's 2, 4 or 8 samples run (1 adjacent lanes, 0 in turn on "
                          "one lane); the autotuner then keeps it")

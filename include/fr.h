@@ -213,9 +213,12 @@ typedef struct {
                                     the compiler allocates differently) with the one
                                     request.  Same images bit for bit.               */
     int32_t batch_kernel;        /* fr_render_batch: 0 persistent kernel with the pixel
-                                    queue, 1 (default) one-ray-per-thread kernel over
-                                    every tile of every request in one launch
-                                    (plain_block threads)                              */
+                                    queue and the lane state machine, 1 one-ray-per-thread
+                                    kernel over every tile of every request in one launch
+                                    (plain_block threads), 2 (default) the same per-pixel
+                                    code in persistent warps, each taking the next tile of
+                                    the launch from the queue head as soon as its lanes
+                                    are done                                           */
     int32_t tile_order;          /* how the one-ray-per-thread kernels lay their 4 x 8
                                     tiles, in launch order, over each image: 0 (default)
                                     rows top to bottom, 1 columns left to right, 2 rows
@@ -247,11 +250,15 @@ FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs);
 
 /* Render n_reqs requests (mixed kinds and sizes) with one kernel launch per 64
  * requests (costliest first: pixels x samples x iteration cap, weighted by
- * fractal and shadows).  Two schedules, picked by fr_tuning.batch_kernel:
- *   1 (default)  one-ray-per-thread kernel over every tile of every request:
- *                each CTA belongs to one request and the hardware block
- *                scheduler hands CTAs to SMs as they free up, so the slow
- *                pixels of different requests overlap;
+ * fractal and shadows).  Three schedules, picked by fr_tuning.batch_kernel:
+ *   2 (default)  one-ray-per-thread code in persistent CTAs over every tile of
+ *                every request: each warp takes the next 32-pixel tile of the
+ *                launch from the queue head as soon as its lanes are done, so
+ *                the slow pixels of different requests overlap and no warp
+ *                waits for the other warps of its CTA;
+ *   1            the same per-pixel code as a grid over every tile of every
+ *                request: each CTA belongs to one request and the hardware
+ *                block scheduler hands CTAs to SMs as they free up;
  *   0            persistent CTAs, each warp pulling pixels from one queue over
  *                all requests and refilling idle lanes as rays finish.
  * Images are the same bit for bit either way (and equal fr_render_julia /
@@ -260,7 +267,7 @@ FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs);
  * one launch per 64 requests, with no host synchronisation and no copy: it can
  * be captured into a CUDA graph and replayed.  `workspace` (device,
  * >= fr_batch_workspace_bytes(n_reqs) bytes, 256-byte aligned) holds the
- * queue heads and is overwritten; two batches in flight at once need two
+ * queue heads of schedules 0 and 2 and is overwritten; two batches in flight at once need two
  * workspaces.  reqs is host memory.  1 <= n_reqs <= 4096.  Errors: FR_EINVAL
  * (also when one launch's 64 requests would need more than 2^31 - 1 CTAs),
  * FR_ENOMEM (workspace too small), FR_ECUDA. */

@@ -1,7 +1,8 @@
 """Autotuner for the launch shapes and schedules of fr_tuning.
 
 For fr_render_batch (tune):
-  batch_kernel       1 one-ray-per-thread kernel over all tiles, 0 persistent kernel
+  batch_kernel       1 one-ray-per-thread kernel over all tiles, 2 persistent warps taking the
+                     tiles from a queue, 0 persistent lane state machine
   plain_block        threads per CTA of the one-ray-per-thread batch kernel
   tile_order         order of the tiles in the launch (rows, columns, rows upward)
   sample_lanes       requests with 2, 4 or 8 samples: their samples on adjacent lanes (1) or
@@ -32,7 +33,7 @@ from . import _ffi as F
 from . import api
 
 SPACE = {
-    "batch_kernel": (1, 0),
+    "batch_kernel": (1, 2, 0),
     "plain_block": (32, 64, 128, 256),
     "tile_order": (0, 1, 2),
     "sample_lanes": (1, 0),
@@ -102,7 +103,7 @@ def _in_use(knob: str, cfg: dict) -> bool:
     if knob in PERSIST_KNOBS:
         return cfg.get("batch_kernel", 0) == 0
     if knob in ("plain_block", "tile_order", "sample_lanes"):
-        return cfg.get("batch_kernel", 0) == 1
+        return cfg.get("batch_kernel", 0) in (1, 2)
     return True
 
 

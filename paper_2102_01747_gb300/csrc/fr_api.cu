@@ -29,7 +29,7 @@ fr_status fail(fr_status st, const char *fmt, ...)
 }
 
 std::mutex g_tuning_mu;
-fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 1, 0, 1};
+fr_tuning g_tuning = {128, 1, 64, 0, 16, 4, 0, 2, 0, 1};
 
 fr_tuning tuning()
 {
@@ -304,7 +304,7 @@ FR_API fr_status fr_set_tuning(const fr_tuning *t)
     if (t->refill_threshold < 1 || t->refill_threshold > 32)
         return fail(FR_EINVAL, "refill_threshold outside 1..32");
     if (t->single_kernel < 0 || t->single_kernel > 2) return fail(FR_EINVAL, "single_kernel must be 0, 1 or 2");
-    if (t->batch_kernel != 0 && t->batch_kernel != 1) return fail(FR_EINVAL, "batch_kernel must be 0 or 1");
+    if (t->batch_kernel < 0 || t->batch_kernel > 2) return fail(FR_EINVAL, "batch_kernel must be 0, 1 or 2");
     if (t->tile_order < 0 || t->tile_order > 2) return fail(FR_EINVAL, "tile_order must be 0, 1 or 2");
     if (t->sample_lanes != 0 && t->sample_lanes != 1) return fail(FR_EINVAL, "sample_lanes must be 0 or 1");
     std::lock_guard<std::mutex> lk(g_tuning_mu);
@@ -399,7 +399,7 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         if (st != FR_OK) return st;
     }
     const fr_tuning tu = tuning();
-    for (fr::DevReq &R : all) set_lanes(R, tu.batch_kernel == 1 ? lanes_per_pixel(tu, R) : 1);
+    for (fr::DevReq &R : all) set_lanes(R, tu.batch_kernel != 0 ? lanes_per_pixel(tu, R) : 1);
 
     // costliest requests first: the cheap ones then fill in behind the costly
     // ones' slow pixels at the end of the launch (outputs travel with their
@@ -431,7 +431,20 @@ FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *w
         A.refill_threshold = tu.refill_threshold;
         A.queue = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 256 * (size_t)chunk);
         fr_status st;
-        if (tu.batch_kernel == 1) {
+        if (tu.batch_kernel == 2) {
+            long long tiles = 0;
+            for (int i = 0; i < n; i++) {
+                A.reqs[i] = all[(size_t)order[(size_t)(first + i)]];
+                A.reqs[i].unit_begin = tiles;
+                A.reqs[i].tile_order = tu.tile_order;
+                tiles += fr::plain_tiles(A.reqs[i]);
+            }
+            A.total_units = tiles;
+            bool phong = false;
+            for (int i = 0; i < n; i++) phong = phong || A.reqs[i].shading != 0;
+            st = launched(fr::launch_batch_refill(A, tu.plain_block, tu.plain_unroll, count, phong,
+                                                  (cudaStream_t)stream));
+        } else if (tu.batch_kernel == 1) {
             long long ctas = 0;
             for (int i = 0; i < n; i++) {
                 A.reqs[i] = all[(size_t)order[(size_t)(first + i)]];

@@ -55,6 +55,12 @@ cudaError_t launch_plain_lanes(const DevReq &R, int block, bool count, cudaStrea
 cudaError_t launch_batch_plain_lanes(const BatchArgs &A, long long ctas, int block, bool count, bool phong,
                                      cudaStream_t s);
 
+// persistent warps over the tiles of A.n_reqs requests, each warp taking the
+// next tile from the queue head A.queue (memset + launch); reqs[r].unit_begin
+// holds request r's first tile, A.total_units the tiles of the launch
+cudaError_t launch_batch_refill(const BatchArgs &A, int block, int unroll, bool count, bool phong, cudaStream_t s);
+cudaError_t launch_batch_refill_lanes(const BatchArgs &A, int block, bool count, bool phong, cudaStream_t s);
+
 // lane-state-machine forward kernel without the queue: one pixel per lane, all tiles launched
 cudaError_t launch_lanes(const BatchArgs &A, int block, int unroll, bool count, bool phong, cudaStream_t s);
 

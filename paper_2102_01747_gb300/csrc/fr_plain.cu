@@ -19,6 +19,17 @@ cudaError_t launch_batch_plain(const BatchArgs &A, long long ctas, int block, in
     return launch_batch_plain_t<1, false, false>(A, ctas, block, s);
 }
 
+cudaError_t launch_batch_refill(const BatchArgs &A, int block, int unroll, bool count, bool phong, cudaStream_t s)
+{
+    for (int i = 0; i < A.n_reqs; i++)
+        if (A.reqs[i].spl > 1) return launch_batch_refill_lanes(A, block, count, phong, s);
+    if (phong) return count ? launch_batch_refill_t<1, true, true>(A, block, s)
+                            : launch_batch_refill_t<1, false, true>(A, block, s);
+    if (count) return launch_batch_refill_t<1, true, false>(A, block, s);
+    if (unroll == 2) return launch_batch_refill_t<2, false, false>(A, block, s);
+    return launch_batch_refill_t<1, false, false>(A, block, s);
+}
+
 // Phong requests run the Phong-capable instantiation at unroll 1
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s)
 {

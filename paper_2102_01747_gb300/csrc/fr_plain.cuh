@@ -135,4 +135,62 @@ static cudaError_t launch_batch_plain_t(const BatchArgs &A, long long ctas, int 
     return cudaGetLastError();
 }
 
+// Persistent warps over every tile of every request of a launch (the
+// fr_render_batch schedule batch_kernel 2): the grid is as many CTAs as fit on
+// the SMs at once, and each warp takes the next tile from one counter (the
+// queue head in the caller's workspace, zeroed before the launch) as soon as
+// its 32 lanes are done with the last, so no warp waits for the other warps
+// of its CTA.  Tiles are numbered over the requests in launch order;
+// reqs[r].unit_begin holds request r's first tile.  A warp's tiles come in
+// increasing order, so its request cursor only moves forward.  The pixels
+// are shade_tile's, so the images are the other schedules' bit for bit.
+template <int U, bool COUNT, bool PHONG, bool LANES = false>
+__global__ void __maxnreg__(72) batch_refill_kernel(const __grid_constant__ BatchArgs A)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)A.total_units;
+    int lo = 0;
+    Counters cnt;
+    if (COUNT)
+        for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
+    for (;;) {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(A.queue, 1ull);
+        g = __shfl_sync(full, g, 0);
+        if (g >= total) break;
+        int r = lo;
+        while (r + 1 < A.n_reqs && (unsigned long long)A.reqs[r + 1].unit_begin <= g) r++;
+        if (COUNT && r != lo) {  // the counters belong to the request they were taken for
+            if (A.reqs[lo].stats) flush_counters(cnt, A.reqs[lo].stats);
+            for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
+        }
+        lo = r;
+        const DevReq &R = A.reqs[lo];
+        const long long tile = (long long)g - R.unit_begin;
+        if (R.kind == 0)
+            shade_tile<0, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
+        else
+            shade_tile<1, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
+    }
+    if (COUNT && A.reqs[lo].stats) flush_counters(cnt, A.reqs[lo].stats);
+}
+
+template <int U, bool COUNT, bool PHONG, bool LANES = false>
+static cudaError_t launch_batch_refill_t(const BatchArgs &A, int block, cudaStream_t s)
+{
+    int dev = 0, sms = 0, fit = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_refill_kernel<U, COUNT, PHONG, LANES>, block,
+                                                           0)) != cudaSuccess)
+        return e;
+    if (fit < 1) return cudaErrorInvalidConfiguration;
+    if ((e = cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    batch_refill_kernel<U, COUNT, PHONG, LANES><<<sms * fit, block, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+
 }  // namespace fr

@@ -39,4 +39,12 @@ cudaError_t launch_batch_plain_lanes(const BatchArgs &A, long long ctas, int blo
                  : launch_batch_plain_t<1, false, false, true>(A, ctas, block, s);
 }
 
+cudaError_t launch_batch_refill_lanes(const BatchArgs &A, int block, bool count, bool phong, cudaStream_t s)
+{
+    if (phong) return count ? launch_batch_refill_t<1, true, true, true>(A, block, s)
+                            : launch_batch_refill_t<1, false, true, true>(A, block, s);
+    return count ? launch_batch_refill_t<1, true, false, true>(A, block, s)
+                 : launch_batch_refill_t<1, false, false, true>(A, block, s);
+}
+
 }  // namespace fr

@@ -181,6 +181,9 @@ def test_tuning_roundtrip_and_checks(F):
     bad = F.fr_tuning(*old)
     bad.refill_threshold = 0
     assert F.fr_set_tuning(bad) == F.FR_EINVAL
+    bad = F.fr_tuning(*old)
+    bad.batch_kernel = 3
+    assert F.fr_set_tuning(bad) == F.FR_EINVAL and "batch_kernel" in F.fr_last_error()
     for v in (-1, 3):
         bad = F.fr_tuning(*old)
         bad.tile_order = v
@@ -229,6 +232,8 @@ def test_autotune_skips_knobs_of_the_other_schedule():
 
     assert autotune._in_use("batch_kernel", {"batch_kernel": 1})
     assert autotune._in_use("plain_block", {"batch_kernel": 1})
+    assert autotune._in_use("plain_block", {"batch_kernel": 2})
+    assert not autotune._in_use("refill_threshold", {"batch_kernel": 2})
     assert not autotune._in_use("refill_threshold", {"batch_kernel": 1})
     assert autotune._in_use("persist_unroll", {"batch_kernel": 0})
     assert not autotune._in_use("plain_block", {"batch_kernel": 0})

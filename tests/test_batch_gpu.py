@@ -1,6 +1,7 @@
 """Batched rendering (fr_render_batch) on the GPU, through both of its
 schedules (batch_kernel 1: one-ray-per-thread kernel over every tile of every
-request; batch_kernel 0: persistent kernel with the pixel queue): per-request
+request; batch_kernel 2: the same code in persistent warps taking tiles from a
+queue; batch_kernel 0: persistent kernel with the pixel queue): per-request
 outputs equal the single-request kernel's, every request matches the oracle,
 and the batch bookkeeping (several launches, workspace, counters) holds."""
 import os
@@ -60,7 +61,7 @@ def tuned(F, **kw):
     return F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
 
 
-@pytest.fixture(params=[1, 0], ids=["batch_kernel1", "batch_kernel0"])
+@pytest.fixture(params=[1, 2, 0], ids=["batch_kernel1", "batch_kernel2", "batch_kernel0"])
 def schedule(request):
     """Run the test under each batch schedule, then restore the tuning."""
     from paper_2102_01747_gb300 import _ffi as F
@@ -71,10 +72,10 @@ def schedule(request):
     F.fr_set_tuning(old)
 
 
-def test_default_schedule_is_the_batch_kernel(api):
+def test_default_schedule_is_the_persistent_warps(api):
     from paper_2102_01747_gb300 import _ffi as F
 
-    assert F.fr_get_tuning().batch_kernel == 1
+    assert F.fr_get_tuning().batch_kernel == 2
 
 
 def test_single_request_equals_plain(api, schedule):
@@ -124,7 +125,8 @@ def test_more_requests_than_one_launch(api):
     dict(batch_kernel=0, persist_unroll=1), dict(batch_kernel=0, persist_unroll=4),
     dict(batch_kernel=0, persist_block=64, persist_ctas_per_sm=1), dict(batch_kernel=0, persist_block=256),
     dict(batch_kernel=1), dict(batch_kernel=1, plain_block=64), dict(batch_kernel=1, plain_block=256),
-    dict(batch_kernel=1, plain_unroll=2)])
+    dict(batch_kernel=1, plain_unroll=2), dict(batch_kernel=2), dict(batch_kernel=2, plain_block=32),
+    dict(batch_kernel=2, plain_block=256, plain_unroll=2), dict(batch_kernel=2, tile_order=1)])
 def test_schedule_does_not_change_images(api, kw):
     from paper_2102_01747_gb300 import _ffi as F
 

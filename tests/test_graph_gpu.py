@@ -68,7 +68,7 @@ def test_single_request_graph(env):
     _replay_matches_eager(torch, [out], call)
 
 
-@pytest.mark.parametrize("batch_kernel", [1, 0])
+@pytest.mark.parametrize("batch_kernel", [1, 2, 0])
 def test_batch_graph(env, batch_kernel):
     torch, F, api = env
     scenes = W.batch_mixed(seed=7, n_requests=70, min_log2=4.0, max_log2=6.5)  # two launches
@@ -85,11 +85,11 @@ def test_batch_graph(env, batch_kernel):
         F.fr_set_tuning(old)
 
 
-@pytest.mark.parametrize("batch_kernel, n_requests", [(1, 5), (0, 70)])
+@pytest.mark.parametrize("batch_kernel, n_requests", [(1, 5), (0, 70), (2, 70)])
 def test_static_batch_graph(env, batch_kernel, n_requests):
     """The allocation-free batch call: its eager call looks up the device array's
     address; captured afterwards, it replays like the others.  Under the
-    persistent schedule (which reads the queue heads in the array) 70 requests
+    persistent schedules (which read the queue heads in the array) 70 requests
     make two launches, using two slots of the array."""
     torch, F, api = env
     scenes = W.batch_mixed(seed=8, n_requests=n_requests, min_log2=4.0, max_log2=6.0)

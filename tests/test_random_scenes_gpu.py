@@ -93,7 +93,7 @@ def test_random_scene_matches_oracle(api, orc, i):
     assert res["ok"], (i, res)
 
 
-@pytest.mark.parametrize("batch_kernel", [1, 0])
+@pytest.mark.parametrize("batch_kernel", [1, 2, 0])
 def test_random_scenes_as_one_batch(api, batch_kernel):
     """All random scenes in one fr_render_batch call give the single-request
     kernel's images bit for bit, under either schedule."""

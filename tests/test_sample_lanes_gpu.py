@@ -91,7 +91,7 @@ def test_sample_layouts_same_bits(mods, case, spp):
             assert np.array_equal(r[k].view(np.uint8), ref[k].view(np.uint8)), (key, k)
 
 
-@pytest.mark.parametrize("batch_kernel", [1, 0])
+@pytest.mark.parametrize("batch_kernel", [1, 2, 0])
 def test_sample_layouts_in_a_batch(mods, batch_kernel):
     """A batch mixing spp 1, 2, 4, 8 and 3 on ragged sizes: with sample lanes
     on, fr_render_batch gives the bits of single requests rendered with them off."""

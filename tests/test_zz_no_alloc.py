@@ -5,10 +5,10 @@ allocation can synchronise the device).  Its scratch memory, one queue head
 per launch of up to 64 requests, lives in a fixed array inside the library.
 
 Called through the C ABI twice in a row, it must give the same images, bit
-for bit, as fr_render_batch given a caller workspace.  Only the persistent
-schedule (batch_kernel 0) reads the queue heads, so that schedule runs here
-with 130 small requests: three launches, which use three different slots of
-the array.  The one-ray-per-thread schedule (the default) is checked too.
+for bit, as fr_render_batch given a caller workspace.  The persistent
+schedules (batch_kernel 0 and 2) read the queue heads, so they run here with
+130 small requests: three launches, which use three different slots of the
+array.  The one-ray-per-thread schedule (the default) is checked too.
 This file sorts last, so a stop-at-first-failure run has already run every
 other test."""
 import numpy as np
@@ -29,7 +29,7 @@ def _set_batch_kernel(F, batch_kernel):
     return keep
 
 
-@pytest.mark.parametrize("batch_kernel, n_requests", [(0, 130), (1, 9)])
+@pytest.mark.parametrize("batch_kernel, n_requests", [(0, 130), (2, 130), (1, 9)])
 def test_static_workspace_batch_matches_workspace_batch(batch_kernel, n_requests):
     import torch
 
