@@ -33,7 +33,7 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # everything included (orbit step, DE epilogue, march update, stencils, camera
 # ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
 # divided by the iterations counted on the same scene (Mandelbulb n = 8 at
-# 1920x1080: 8.534 G / 50.88 M = 167.7; Julia p = 2 at 256x256:
+# 1920x1080: 8.532 G / 50.88 M = 167.7; Julia p = 2 at 256x256:
 # 364.9 M / 10.27 M = 35.6; Mandelbulb powers 2..10 at 960x540, the same
 # scene and camera, one request each).  The degree-3 Julia figure is the
 # degree-2 one scaled by the ratio of their orbit-step arithmetic (28 / 24);
@@ -59,12 +59,12 @@ ALG_PER_DE = {"julia": 19, "bulb": 17}
 # configuration launches), from the ncu capture of the same command
 # (dram__bytes_read.sum + dram__bytes_write.sum); the frame's 16.6 MB of
 # stores are still in the 129 MB L2 when the kernel ends.
-TRAFFIC = {("bulb_1080p", "plain_kernel"): 1393152 + 33024, ("bulb_1080p", "batch_plain_kernel"): 72448 + 768}
+TRAFFIC = {("bulb_1080p", "plain_kernel"): 46336 + 1024, ("bulb_1080p", "batch_plain_kernel"): 82432 + 0}
 # The kernel sources the two tables above were counted on (sha256 over these
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
 COUNTED_SOURCES = ("fr_device.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
-COUNTED_SHA = "d05b73bf8112938f984516a48a8282f500e7eafad3383be3ccd6ac141ba6f9d5"
+COUNTED_SHA = "e94c815f439ab64f207585b5ed3fa0eda2530ee9394e9ee4083de7f1bb7eb62e"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 
 

@@ -449,7 +449,7 @@ __device__ __forceinline__ float julia_de3(const float4 c, float slice_w, int ma
 }
 
 template <int U>
-__device__ __forceinline__ float bulb_de(int n, int max_iter, float esc2, float3 c, int alg, int &trips)
+__device__ __forceinline__ float bulb_orbit(int n, int max_iter, float esc2, float3 c, int alg, int &trips)
 {
     Orbit o;
     bulb_init(o, c);
@@ -467,6 +467,24 @@ __device__ __forceinline__ float bulb_de(int n, int max_iter, float esc2, float3
     return bulb_dist(o);
 }
 
+// The orbit loop is copied for each form of the step (transcendental or de
+// Moivre) and, in each, for the paper's power n = 8 compiled with n a
+// constant (the straight-line r^7), so that the loop tests neither; the other
+// powers share the copy with n at run time.  Every copy makes the same
+// products in the same order.
+template <int U>
+__device__ __forceinline__ float bulb_de(int n, int max_iter, float esc2, float3 c, int alg, int &trips)
+{
+    if (alg) {
+        if (n == 8) return bulb_orbit<U>(8, max_iter, esc2, c, 1, trips);
+        return bulb_orbit<U>(n, max_iter, esc2, c, 1, trips);
+    }
+    if (n == 8) return bulb_orbit<U>(8, max_iter, esc2, c, 0, trips);
+    return bulb_orbit<U>(n, max_iter, esc2, c, 0, trips);
+}
+
+// KIND: 0 the Julia set, 1 the Mandelbulb, 2 the Mandelbulb of a request
+// whose power is 8 (the kernel then holds no code for other powers)
 template <int KIND, int U>
 __device__ __forceinline__ float de(const DevReq &R, float3 p, int &trips)
 {
@@ -474,7 +492,7 @@ __device__ __forceinline__ float de(const DevReq &R, float3 p, int &trips)
         if (R.power == 2) return julia_de2<U>(R.c, R.slice_w, R.max_iter, R.esc2, p, trips);
         return julia_de3<U>(R.c, R.slice_w, R.max_iter, R.esc2, p, trips);
     }
-    return bulb_de<U>(R.power, R.max_iter, R.esc2, p, R.bulb_alg, trips);
+    return bulb_de<U>(KIND == 2 ? 8 : R.power, R.max_iter, R.esc2, p, R.bulb_alg, trips);
 }
 
 // ------------------------------------------------------------------ orbit traps

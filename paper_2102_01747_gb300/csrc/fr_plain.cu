@@ -30,7 +30,9 @@ cudaError_t launch_batch_refill(const BatchArgs &A, int block, int unroll, bool 
     return launch_batch_refill_t<1, false, false>(A, block, s);
 }
 
-// Phong requests run the Phong-capable instantiation at unroll 1
+// Phong requests run the Phong-capable instantiation at unroll 1; Mandelbulb
+// requests of the paper's power 8 (not counting) an instantiation for that
+// power
 cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cudaStream_t s)
 {
     if (R.spl > 1) return launch_plain_lanes(R, block, count, s);
@@ -38,7 +40,8 @@ cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cud
     if (R.shading) {
         if (R.kind == 0)
             return count ? launch_plain_t<0, 1, true, true>(R, block, s) : launch_plain_t<0, 1, false, true>(R, block, s);
-        return count ? launch_plain_t<1, 1, true, true>(R, block, s) : launch_plain_t<1, 1, false, true>(R, block, s);
+        if (count) return launch_plain_t<1, 1, true, true>(R, block, s);
+        return R.power == 8 ? launch_plain_t<2, 1, false, true>(R, block, s) : launch_plain_t<1, 1, false, true>(R, block, s);
     }
     if (count) return R.kind == 0 ? launch_plain_t<0, 1, true>(R, block, s)
                                   : launch_plain_t<1, 1, true>(R, block, s);
@@ -46,6 +49,11 @@ cudaError_t launch_plain(const DevReq &R, int block, int unroll, bool count, cud
         if (unroll == 4) return launch_plain_t<0, 4, false>(R, block, s);
         if (unroll == 2) return launch_plain_t<0, 2, false>(R, block, s);
         return launch_plain_t<0, 1, false>(R, block, s);
+    }
+    if (R.power == 8) {
+        if (unroll == 4) return launch_plain_t<2, 4, false>(R, block, s);
+        if (unroll == 2) return launch_plain_t<2, 2, false>(R, block, s);
+        return launch_plain_t<2, 1, false>(R, block, s);
     }
     if (unroll == 4) return launch_plain_t<1, 4, false>(R, block, s);
     if (unroll == 2) return launch_plain_t<1, 2, false>(R, block, s);
