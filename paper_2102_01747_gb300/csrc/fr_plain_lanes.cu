@@ -2,7 +2,8 @@
 // pixel's 2, 4 or 8 samples on adjacent lanes (LANES, render_pixel_lanes), for
 // requests with R.spl > 1 (a translation unit of its own so that it compiles
 // in parallel with the rest).  Unroll depth 1; Phong requests take the
-// Phong-capable instantiation, the Mandelbulb's analytic normal the BAN one.
+// Phong-capable instantiation, the Mandelbulb's analytic normal the BAN one,
+// and Lambert Mandelbulb requests of the power 8 one compiled for that power.
 #include "fr_plain.cuh"
 
 namespace fr {
@@ -26,8 +27,9 @@ cudaError_t launch_plain_lanes(const DevReq &R, int block, bool count, cudaStrea
     if (R.shading)
         return count ? launch_plain_t<1, 1, true, true, false, true>(R, block, s)
                      : launch_plain_t<1, 1, false, true, false, true>(R, block, s);
-    return count ? launch_plain_t<1, 1, true, false, false, true>(R, block, s)
-                 : launch_plain_t<1, 1, false, false, false, true>(R, block, s);
+    if (count) return launch_plain_t<1, 1, true, false, false, true>(R, block, s);
+    return R.power == 8 ? launch_plain_t<2, 1, false, false, false, true>(R, block, s)
+                        : launch_plain_t<1, 1, false, false, false, true>(R, block, s);
 }
 
 cudaError_t launch_batch_plain_lanes(const BatchArgs &A, long long ctas, int block, bool count, bool phong,
