@@ -64,7 +64,7 @@ TRAFFIC = {("bulb_1080p", "plain_kernel"): 46336 + 1024, ("bulb_1080p", "batch_p
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
 COUNTED_SOURCES = ("fr_device.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
-COUNTED_SHA = "e94c815f439ab64f207585b5ed3fa0eda2530ee9394e9ee4083de7f1bb7eb62e"
+COUNTED_SHA = "be408144e99efcb5360346aa42a770113dd5b69ccf0930c5dd6b971b06396bf5"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 
 

@@ -659,10 +659,10 @@ __device__ __forceinline__ float3 finish_normal(float3 g, float3 rd)
 // one-ray-per-thread kernel (48 -> 64 for the Mandelbulb), a cost every pixel
 // pays, while three passes cost hit pixels three orbits, one fewer than the
 // tetrahedral stencil.  Each pass repeats the same operations on w, so the
-// orbit, its length and the stop are the same in all three.
-__device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, float3 x, float3 rd, int &trips)
+// orbit, its length and the stop are the same in all three.  n is the
+// request's power, the literal 8 in kernels compiled for that power.
+__device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, int n, float3 x, float3 rd, int &trips)
 {
-    const int n = R.power;
     const float nf = (float)n;
     float3 g = v3(0.0f, 0.0f, 0.0f);
     int i = 0;

@@ -345,7 +345,7 @@ __device__ void advance(Lane &S, const DevReq &R, float d, PixCount &pc)
     if (R.normal_mode == 2) {  // analytic normal: one orbit with tangents, no stencil
         int trips;
         S.g = R.kind == 0 ? julia_analytic_normal(R, S.x, S.rd, trips)
-                          : bulb_analytic_normal(R, S.x, S.rd, trips);
+                          : bulb_analytic_normal(R, R.power, S.x, S.rd, trips);
         if (COUNT) {
             pc.v[kStatNormalDE] += 1;
             pc.v[kStatOrbit] += trips;

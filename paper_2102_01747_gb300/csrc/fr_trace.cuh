@@ -49,7 +49,7 @@ __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd
     if ((KIND == 0 || BAN) && R.normal_mode == 2) {
         int trips;
         const float3 n = KIND == 0 ? julia_analytic_normal(R, x, rd, trips)
-                                   : bulb_analytic_normal(R, x, rd, trips);
+                                   : bulb_analytic_normal(R, KIND == 2 ? 8 : R.power, x, rd, trips);
         if (COUNT) {
             cnt.v[kStatNormalDE] += 1;
             cnt.v[kStatOrbit] += trips;
