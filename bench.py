@@ -64,7 +64,7 @@ TRAFFIC = {("bulb_1080p", "plain_kernel"): 46336 + 1024, ("bulb_1080p", "batch_p
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
 COUNTED_SOURCES = ("fr_device.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
-COUNTED_SHA = "be408144e99efcb5360346aa42a770113dd5b69ccf0930c5dd6b971b06396bf5"
+COUNTED_SHA = "64e75fdf3139fedeeb452f35879a4f1e75765a6064e16d94f3490521baabd7a5"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 
 

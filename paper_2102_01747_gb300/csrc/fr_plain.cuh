@@ -52,7 +52,7 @@ __device__ __forceinline__ void tile_pixel(const DevReq &R, long long tile, int 
 // turn; LANES true: the samples of a pixel on R.spl adjacent lanes), called by
 // all 32 lanes of the warp; the packed colour and depth of finished pixels go
 // to the warp's quad store.
-template <int KIND, int U, bool COUNT, bool PHONG, bool BAN, bool LANES>
+template <int KIND, int U, bool COUNT, bool PHONG, int BAN, bool LANES>
 __device__ __forceinline__ void shade_tile(const DevReq &R, long long tile, Counters &cnt)
 {
     const int lane = threadIdx.x & 31;
@@ -70,8 +70,9 @@ __device__ __forceinline__ void shade_tile(const DevReq &R, long long tile, Coun
     }
 }
 
-// BAN: compiled with the Mandelbulb's analytic normal (normal_at)
-template <int KIND, int U, bool COUNT, bool PHONG, bool BAN, bool LANES = false>
+// BAN: compiled with the Mandelbulb's analytic normal (normal_at; 1 inline,
+// 2 out of line)
+template <int KIND, int U, bool COUNT, bool PHONG, int BAN, bool LANES = false>
 __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevReq R)
 {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(256) plain_kernel(const __grid_constant__ DevR
     if (COUNT) flush_counters(cnt, R.stats);
 }
 
-template <int KIND, int U, bool COUNT, bool PHONG = false, bool BAN = false, bool LANES = false>
+template <int KIND, int U, bool COUNT, bool PHONG = false, int BAN = 0, bool LANES = false>
 static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 {
     const long long threads = plain_tiles(R) * 32;
@@ -98,7 +99,7 @@ static cudaError_t launch_plain_t(const DevReq &R, int block, cudaStream_t s)
 // CTAs to SMs as they free up, so the requests' slow pixels overlap instead of
 // each launch waiting for its own.  tile_begin of request r (in CTAs) is kept
 // in reqs[r].unit_begin.
-// Always compiled with the Mandelbulb's analytic normal, and held to 72
+// Always compiled with the Mandelbulb's analytic normal (out of line), and held to 72
 // registers (at most 256 threads per block, as fr_set_tuning enforces): left
 // to itself the compiler takes 80, with which the 64-request mixed batch runs
 // 36.0 ms against 33.3 (64 registers: 33.5).  fr_render_* can also launch it
@@ -122,9 +123,9 @@ __global__ void __maxnreg__(72) batch_plain_kernel(const __grid_constant__ Batch
     if (COUNT)
         for (int k = 0; k < kNStats; k++) cnt.v[k] = 0;
     if (R.kind == 0)
-        shade_tile<0, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
+        shade_tile<0, U, COUNT, PHONG, 2, LANES>(R, tile, cnt);
     else
-        shade_tile<1, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
+        shade_tile<1, U, COUNT, PHONG, 2, LANES>(R, tile, cnt);
     if (COUNT && R.stats) flush_counters(cnt, R.stats);
 }
 
@@ -169,9 +170,9 @@ __global__ void __maxnreg__(72) batch_refill_kernel(const __grid_constant__ Batc
         const DevReq &R = A.reqs[lo];
         const long long tile = (long long)g - R.unit_begin;
         if (R.kind == 0)
-            shade_tile<0, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
+            shade_tile<0, U, COUNT, PHONG, 2, LANES>(R, tile, cnt);
         else
-            shade_tile<1, U, COUNT, PHONG, true, LANES>(R, tile, cnt);
+            shade_tile<1, U, COUNT, PHONG, 2, LANES>(R, tile, cnt);
     }
     if (COUNT && A.reqs[lo].stats) flush_counters(cnt, A.reqs[lo].stats);
 }

@@ -42,14 +42,17 @@ __device__ __forceinline__ bool march(const DevReq &R, float3 ro, float3 rd, flo
 // gradient gives -rd.  The Mandelbulb's analytic normal is compiled only into
 // the BAN instantiations (requests that ask for it are launched there): its
 // orbit is a third inlined copy of the trig step, and carried in every kernel
-// it slowed the Phong frame by 7 % (instruction fetch).
-template <int KIND, int U, bool COUNT, bool BAN>
+// it slowed the Phong frame by 7 % (instruction fetch).  BAN 1 inlines it (the
+// single-request kernels for such requests), BAN 2 calls it out of line (the
+// batch kernels, which carry it for every launch).
+template <int KIND, int U, bool COUNT, int BAN>
 __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd, Counters &cnt)
 {
     if ((KIND == 0 || BAN) && R.normal_mode == 2) {
         int trips;
         const float3 n = KIND == 0 ? julia_analytic_normal(R, x, rd, trips)
-                                   : bulb_analytic_normal(R, KIND == 2 ? 8 : R.power, x, rd, trips);
+                                   : BAN == 2 ? bulb_analytic_normal_ool(R, KIND == 2 ? 8 : R.power, x, rd, trips)
+                                                 : bulb_analytic_normal(R, KIND == 2 ? 8 : R.power, x, rd, trips);
         if (COUNT) {
             cnt.v[kStatNormalDE] += 1;
             cnt.v[kStatOrbit] += trips;
@@ -80,7 +83,7 @@ __device__ __forceinline__ float3 normal_at(const DevReq &R, float3 x, float3 rd
 // single call site for all DE evaluations (one loop whose trips pick the point
 // by phase) measured slower again (1.10 ms; Julia 256^2 0.149 against
 // 0.117 ms): its phase bookkeeping costs more than the smaller code saves.
-template <int KIND, int U, bool COUNT, bool BAN>
+template <int KIND, int U, bool COUNT, int BAN>
 __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float3 rd, float &t_hit,
                                                uint32_t &flags, float3 &xhit, Counters &cnt)
 {
@@ -134,7 +137,7 @@ __device__ __forceinline__ float4 trace_sample(const DevReq &R, float3 ro, float
 // by Fresnel-Schlick in shade_phong.  The two hits' normals share one stencil
 // call, so the DE is still inlined twice.  Kept apart from the Lambert-only
 // loop above, which holds fewer live values.
-template <int KIND, int U, bool COUNT, bool BAN>
+template <int KIND, int U, bool COUNT, int BAN>
 __device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro, float3 rd, float &t_hit,
                                                      uint32_t &flags, float3 &xhit, Counters &cnt)
 {
@@ -207,7 +210,7 @@ __device__ __forceinline__ float4 trace_sample_phong(const DevReq &R, float3 ro,
 // warp's quad store (store_rgba8_depth).  PHONG compiles the Phong +
 // mirror-ray path in (requests still choose it with R.shading); without it the
 // Lambert-only code keeps fewer registers.
-template <int KIND, int U, bool COUNT, bool PHONG, bool BAN = false>
+template <int KIND, int U, bool COUNT, bool PHONG, int BAN = 0>
 __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Counters &cnt, uint32_t &c8,
                                              float &depth)
 {
@@ -251,7 +254,7 @@ __device__ __forceinline__ void render_pixel(const DevReq &R, int px, int py, Co
 // give the same bits; its results are the pixel's.  `valid`: the pixel lies
 // inside the image.  (Kernels of their own: carried in the one-lane kernels,
 // this code cost the 1080p frame 2.5 %.)
-template <int KIND, int U, bool COUNT, bool PHONG, bool BAN = false>
+template <int KIND, int U, bool COUNT, bool PHONG, int BAN = 0>
 __device__ __forceinline__ void render_pixel_lanes(const DevReq &R, int px, int py, int sample, bool valid,
                                                    Counters &cnt, uint32_t &c8, float &depth)
 {
