@@ -257,8 +257,21 @@ def cpu_baseline(scenes, budget_s: float = 12.0):
         rays += _oracle_rays(oracle, scenes, samples, threads)
         dt += time.perf_counter() - t1
         reps += 1
-    return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": "%s of each image, %d pass%s, %.1f s" % (_stride_words(stride), reps, "" if reps == 1 else "es", dt)}
+    out = {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+           "sample": "%s of each image, %d pass%s, %.1f s" % (_stride_words(stride), reps, "" if reps == 1 else "es", dt)}
+    # the same oracle on one thread, over a sparser sample of the same images
+    one_stride = stride * max(1, threads)
+    while True:
+        samples = _oracle_sample(scenes, one_stride)
+        t0 = time.perf_counter()
+        rays1 = _oracle_rays(oracle, scenes, samples, 1)
+        dt1 = time.perf_counter() - t0
+        if dt1 >= budget_s / 8 or one_stride == 1:
+            break
+        one_stride = max(1, int(one_stride * dt1 / (budget_s / 4)) if dt1 > 0 else 1)
+    out["one_thread"] = {"value": rays1 / dt1 / 1e6, "unit": "Mrays/s", "cores": 1,
+                         "sample": "%s of each image, %.1f s" % (_stride_words(one_stride), dt1)}
+    return out
 
 
 class Renderer:
