@@ -194,11 +194,15 @@ def _oracle_sample(scenes, stride):
             for s in scenes]
 
 
-def _oracle_rays(oracle, scenes, samples, threads):
+def _oracle_rays(oracle, scenes, samples, threads, des=None):
+    """Rays the oracle traced for the sampled pixels; DE calls are added to des[0]."""
     rays = 0
     for s, px in zip(scenes, samples):
         r = oracle.render(s, pixels=px, precision="f32", threads=threads)
-        rays += len(px) * s["camera"]["spp"] + int(r["stats"][:, 4].sum()) + int(r["stats"][:, 6].sum())
+        st = r["stats"]
+        rays += len(px) * s["camera"]["spp"] + int(st[:, 4].sum()) + int(st[:, 6].sum())
+        if des is not None:  # primary, normal, shadow and reflection DE calls
+            des[0] += int(st[:, 0].sum() + st[:, 1].sum() + st[:, 2].sum() + st[:, 5].sum())
     return rays
 
 
@@ -217,9 +221,9 @@ def run_reference(args, scenes, desc, rank, world):
     for _ in range(args.warmup):  # untimed warm-up steps on the same sample
         _oracle_rays(oracle, scenes, samples, threads)
     t0 = time.perf_counter()
-    rays = 0
+    rays, des = 0, [0]
     for _ in range(args.steps):
-        rays += _oracle_rays(oracle, scenes, samples, threads)
+        rays += _oracle_rays(oracle, scenes, samples, threads, des)
     dt = time.perf_counter() - t0
     value = rays / dt / 1e6
     sample = "%s of each image (%d pixels per step)" % (_stride_words(stride), sum(map(len, samples)))
@@ -230,7 +234,7 @@ def run_reference(args, scenes, desc, rank, world):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc},
         "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "de_evals_per_s": des[0] / dt},
         "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -245,8 +249,9 @@ def cpu_baseline(scenes, budget_s: float = 12.0):
     stride = 256
     while True:
         samples = _oracle_sample(scenes, stride)
+        des = [0]
         t0 = time.perf_counter()
-        rays = _oracle_rays(oracle, scenes, samples, threads)
+        rays = _oracle_rays(oracle, scenes, samples, threads, des)
         dt = time.perf_counter() - t0
         if dt >= budget_s / 3 or stride == 1:
             break
@@ -254,10 +259,11 @@ def cpu_baseline(scenes, budget_s: float = 12.0):
     reps = 1
     while dt * (reps + 1) / reps < budget_s and reps < 20 and dt < budget_s:
         t1 = time.perf_counter()
-        rays += _oracle_rays(oracle, scenes, samples, threads)
+        rays += _oracle_rays(oracle, scenes, samples, threads, des)
         dt += time.perf_counter() - t1
         reps += 1
     out = {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+           "de_evals_per_s": des[0] / dt,
            "sample": "%s of each image, %d pass%s, %.1f s" % (_stride_words(stride), reps, "" if reps == 1 else "es", dt)}
     # the same oracle on one thread, over a sparser sample of the same images
     one_stride = stride * max(1, threads)
