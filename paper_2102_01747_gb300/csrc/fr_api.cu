@@ -354,6 +354,7 @@ FR_API fr_status fr_render_julia(const fr_julia_params *params, const fr_plane *
                                  const fr_camera *camera, const fr_light *light, const fr_image *out,
                                  void *stream)
 {
+    fr::NvtxRange range("fr_render_julia");
     fr::DevReq R;
     std::memset(&R, 0, sizeof R);
     fr_status st = resolve_julia(R, params);
@@ -366,6 +367,7 @@ FR_API fr_status fr_render_mandelbulb(const fr_bulb_params *params, const fr_pla
                                       const fr_camera *camera, const fr_light *light,
                                       const fr_image *out, void *stream)
 {
+    fr::NvtxRange range("fr_render_mandelbulb");
     fr::DevReq R;
     std::memset(&R, 0, sizeof R);
     fr_status st = resolve_bulb(R, params);
@@ -384,6 +386,7 @@ FR_API size_t fr_batch_workspace_bytes(int32_t n_reqs)
 FR_API fr_status fr_render_batch(const fr_request *reqs, int32_t n_reqs, void *workspace,
                                  size_t ws_bytes, void *stream)
 {
+    fr::NvtxRange range("fr_render_batch");
     if (!reqs) return fail(FR_EINVAL, "requests is NULL");
     if (n_reqs < 1 || n_reqs > 4096) return fail(FR_EINVAL, "n_reqs %d outside 1..4096", n_reqs);
     if (!workspace) return fail(FR_EINVAL, "workspace is NULL");
@@ -522,6 +525,7 @@ FR_API fr_status fr_render_backward(const fr_julia_params *params, const fr_plan
                                     const fr_camera *camera, const fr_light *light, const float *saved,
                                     const float *d_rgba, const float *d_depth, float *grad, void *stream)
 {
+    fr::NvtxRange range("fr_render_backward");
     fr::BwdArgs A;
     const fr_status st = resolve_backward(A, params, plane, camera, light, saved, d_rgba, d_depth, grad);
     if (st != FR_OK) return st;
@@ -533,6 +537,7 @@ FR_API fr_status fr_render_backward_mandelbulb(const fr_bulb_params *params, con
                                                const float *saved, const float *d_rgba, const float *d_depth,
                                                float *grad, void *workspace, size_t ws_bytes, void *stream)
 {
+    fr::NvtxRange range("fr_render_backward_mandelbulb");
     if (workspace && !aligned(workspace, 16)) return fail(FR_EINVAL, "workspace must be 16-byte aligned");
     if (workspace && ws_bytes < fr_backward_workspace_bytes())
         return fail(FR_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, fr_backward_workspace_bytes());
@@ -563,6 +568,7 @@ FR_API fr_status fr_render_backward_ws(const fr_julia_params *params, const fr_p
                                        const float *d_rgba, const float *d_depth, float *grad,
                                        void *workspace, size_t ws_bytes, void *stream)
 {
+    fr::NvtxRange range("fr_render_backward_ws");
     if (!workspace) return fail(FR_EINVAL, "workspace is NULL");
     if (!aligned(workspace, 16)) return fail(FR_EINVAL, "workspace must be 16-byte aligned");
     if (ws_bytes < fr_backward_workspace_bytes())

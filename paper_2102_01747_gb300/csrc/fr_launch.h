@@ -2,10 +2,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "fr_device.cuh"
 
 namespace fr {
+
+// An NVTX range over one C-ABI call, so that a profiler's timeline shows the
+// calls beside their kernels (NVTX v3 is header-only; without a tool attached
+// a push and a pop cost two indirect calls).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // requests per batch launch (either schedule): the table rides in the kernel parameters
 // (64 x sizeof(DevReq) stays well inside the 32 KB parameter limit)

@@ -48,6 +48,7 @@ extern "C" {
 
 FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, void *stream)
 {
+    fr::NvtxRange range("fr_render_batch_static");
     char msg[160];
     if (!reqs) return fr::set_error(FR_EINVAL, "requests is NULL");
     if (n_reqs < 1 || n_reqs > kStaticMaxRequests) {
