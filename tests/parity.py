@@ -5,7 +5,11 @@ float, the GPU with fused multiply-adds and the CUDA math library, the oracle
 with the host libm and no fusion):
   - hit / miss agreement on >= 99.5% of pixels (alpha > 0 counts as a hit);
   - relative depth error <= 1e-3 on >= 99% of the pixels both sides hit;
-  - every RGB channel within 3/255 on >= 99% of pixels.
+  - every RGB channel within 3/255 on >= 99% of pixels;
+  - no depth is NaN or -inf (a hit has a finite depth, a miss +inf), and the
+    GPU's and the oracle's depths are finite on the same pixels on >= 99.5%
+    of them, so no NaN slips past the depth comparison.  (The alpha channel is
+    the hit flag only where the background is transparent.)
 """
 import numpy as np
 
@@ -38,6 +42,9 @@ def compare(gpu_rgba8, gpu_depth, orc_rgba8, orc_depth):
         "depth_ok": depth_ok,
         "rgb_ok": rgb_ok,
         "depth_rel_p50": float(np.median(rel)) if both.any() else 0.0,
+        "bad_depths": int(np.sum(np.isnan(gd)) + np.sum(np.isneginf(gd))),
+        "finite_agree": float(np.mean(np.isfinite(gd) == np.isfinite(od))) if len(gd) else 1.0,
     }
-    res["ok"] = hit_agree >= HIT_AGREE and depth_ok >= DEPTH_FRAC and rgb_ok >= RGB_FRAC
+    res["ok"] = (hit_agree >= HIT_AGREE and depth_ok >= DEPTH_FRAC and rgb_ok >= RGB_FRAC
+                 and res["bad_depths"] == 0 and res["finite_agree"] >= HIT_AGREE)
     return res

@@ -117,7 +117,8 @@ def test_extreme_shapes(api, orc, w, h):
     assert res["ok"], res
 
 
-@pytest.mark.parametrize("path", ["plain", "lanes", "single_via_batch_kernel", "batch_kernel", "batch_persistent"])
+@pytest.mark.parametrize("path", ["plain", "lanes", "single_via_batch_kernel", "batch_kernel", "batch_refill",
+                                  "batch_persistent"])
 def test_largest_image(api, orc, path):
     """46340 x 46340 = 2,147,395,600 pixels, just under the 2^31 limit of
     width*height*spp (its padded 4 x 8 tiles hold more than 2^31 pixel slots):
@@ -133,7 +134,7 @@ def test_largest_image(api, orc, path):
     old = F.fr_get_tuning()
     t = F.fr_tuning(*[getattr(old, n) for n, _ in F.fr_tuning._fields_])
     t.single_kernel = {"lanes": 1, "single_via_batch_kernel": 2}.get(path, 0)
-    t.batch_kernel = 0 if path == "batch_persistent" else 1
+    t.batch_kernel = {"batch_persistent": 0, "batch_refill": 2}.get(path, 1)
     assert F.fr_set_tuning(t) == F.FR_OK
     try:
         if path.startswith("batch_"):
