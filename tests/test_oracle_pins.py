@@ -417,6 +417,28 @@ def test_de_lower_bound_3d(orc, kind):
     assert 1.1 <= np.median(dbf / d) <= 3.0
 
 
+@pytest.mark.parametrize("p", [2, 3])
+def test_julia_slice_is_a_rotation(orc, p):
+    """With c in span{1, i}, z -> z^p + c commutes with every rotation of the
+    (j, k) plane (z^p keeps the direction of z's imaginary part; c has no j or
+    k part), so |z_n| and |z_n'| are invariant: the DE at (x, y, z) on the
+    slice w = s equals the DE at (x, y, sqrt(z^2 + s^2)) on the slice w = 0."""
+    rng = np.random.default_rng(32 + p)
+    base = W.julia_256(8, 8)
+    base["p"], base["c"] = p, ((-0.2, 0.6, 0.0, 0.0) if p == 2 else (-0.1, 0.55, 0.0, 0.0))
+    same = close = 0
+    for _ in range(40):
+        sw = float(rng.uniform(-0.7, 0.7))
+        pts = rng.uniform(-1.2, 1.2, (20, 3))
+        rot = np.c_[pts[:, :2], np.sqrt(pts[:, 2] ** 2 + sw * sw)]
+        d1, n1, t1, _ = orc.de(dict(base, slice_w=sw), pts)
+        d0, n0, t0, _ = orc.de(dict(base, slice_w=0.0), rot)
+        ok = (n1 == n0) & (t1 == t0)
+        same += int(ok.sum())
+        close += int(np.sum(ok & (np.abs(d1 - d0) <= 1e-9 * np.maximum(np.abs(d0), 1e-12))))
+    assert same >= 0.98 * 800 and close == same
+
+
 # ------------------------------------------------ gradient schemes (Eq. 5)
 def test_tetra_gradient_exact_on_affine(orc):
     """Sum nu_i = 0 and sum (nu_i)_x nu_i = (4, 0, 0) make Eq. 5 exact on affine
@@ -441,6 +463,27 @@ def test_central_gradient_exact_on_quadratic(orc):
         n = orc.normal_field(2, np.r_[A.ravel(), g], p, orc.NORMAL_CENTRAL, h)
         grad = (A + A.T) @ p + g
         assert np.allclose(n, grad / np.linalg.norm(grad), rtol=0, atol=1e-8)
+
+
+def test_tetra_default_step_follows_eps(orc):
+    """With normal_h = 0 the tetrahedral stencil takes the listing's step
+    h = 0.5773 eps.  The c = 0 Julia set's DE is d = r log(r) / 2 whatever the
+    escape count (z_n = r^(2^n), |z_n'| = 2^n r^(2^n - 1)), so the exact normal
+    is x / |x|.  On a radial field Eq. 5 errs by a tangential term of order h
+    (the tetrahedron's third moment, sum nu (nu . u)^2, is nonzero off its
+    axes), so the normal's error is small and falls tenfold with eps."""
+    rng = np.random.default_rng(31)
+    dirs = rng.standard_normal((60, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    errs = {}
+    for eps in (1e-3, 1e-4):
+        s = W.julia_256(8, 8)
+        s["c"] = (0.0, 0.0, 0.0, 0.0)
+        s["normal_mode"], s["normal_h"], s["eps"] = "tetra", 0.0, eps
+        errs[eps] = np.array([np.linalg.norm(orc.normal_scene(s, 1.5 * u) - u) for u in dirs])
+    assert np.max(errs[1e-3]) < 2e-3
+    ratio = np.median(errs[1e-3] / np.maximum(errs[1e-4], 1e-300))
+    assert 7.0 < ratio < 14.0, ratio
 
 
 def test_zero_gradient_falls_back_to_view(orc):
