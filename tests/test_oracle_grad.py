@@ -95,6 +95,25 @@ def test_implicit_gradient_matches_fd_per_pixel(orc, normal):
             assert np.all(g[:, :4] == 0)
 
 
+def test_shadowed_gradient_matches_fd_per_pixel(orc):
+    """With shadow rays the lit surface pixels carry the diffuse term and the
+    shadowed ones only the ambient: per pixel at a converged march, both kinds
+    against the finite differences of the render (the pixel's state, shadow
+    included, unchanged at theta +- h)."""
+    size = 40
+    s, _ = W.diff_julia(W.BASE_SEED, size, size)
+    s["eps"], s["max_steps"] = 1e-9, 5000
+    s["light"] = dict(s["light"], shadows=True)
+    d_rgba, d_depth = cotangents(size * size, seed=3)
+    fd, mask, base = fd_per_pixel(orc, s, d_rgba, d_depth, 1e-6)
+    for kind, sel in (("lit", base["flags"] == 1), ("shadowed", base["flags"] == 5)):
+        idx = np.flatnonzero(mask & sel)
+        assert len(idx) > 30, (kind, len(idx))
+        g = implicit_per_pixel(orc, s, d_rgba, d_depth, idx)
+        err = np.linalg.norm(fd[idx] - g, axis=1) / np.maximum(np.linalg.norm(fd[idx], axis=1), 1e-12)
+        assert np.mean(err < 0.01) >= 0.99, (kind, np.quantile(err, [0.5, 0.99]))
+
+
 def test_implicit_gradient_fd_moderate_eps(orc):
     """eps = 1e-5, h = 1e-4: the march is converged well enough for 95% of the
     surface pixels to agree within 5%."""
