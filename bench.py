@@ -63,7 +63,7 @@ TRAFFIC = {("bulb_1080p", "plain_kernel"): 46336 + 1024, ("bulb_1080p", "batch_p
 # The kernel sources the two tables above were counted on (sha256 over these
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
-COUNTED_SOURCES = ("fr_device.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
+COUNTED_SOURCES = ("fr_device.cuh", "fr_math.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
 COUNTED_SHA = "7e6ad19bd05fa59fcc05b75ab5b573bcd7cdca9ef137d73c059dea41cc3f535b"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 

@@ -3,9 +3,11 @@
 // One request is a DevReq: the public parameter structs of include/fr.h resolved
 // on the host into what the kernels read (camera basis, normalised light,
 // squared radii, output pointers).  Every routine here computes in FP32 with
-// the accurate CUDA math library (no --use_fast_math, no approximate __xxxf
-// intrinsics) and spells out every rounding step (mul/add/sub/dvd, fmaf), so
-// that all kernels compute the same bits for the same ray.
+// the accurate CUDA math library or, for the Mandelbulb power's angles, the
+// routines of fr_math.cuh (same error bounds, measured; no --use_fast_math,
+// no approximate __xxxf intrinsics) and spells out every rounding step
+// (mul/add/sub/dvd, fmaf), so that all kernels compute the same bits for the
+// same ray.
 //
 // Paper passages (da Silva, Novello, Lopes, Velho, "Real-time rendering of
 // complex fractals"):
@@ -25,6 +27,8 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "fr_math.cuh"
 
 namespace fr {
 
@@ -258,9 +262,6 @@ __device__ __forceinline__ float julia_dist(const Orbit &o)
     return mul(mul(0.25f, logf(o.m)), sqrtf(dvd(o.m, o.dz)));
 }
 
-// 1 / pi rounded to float
-constexpr float kInvPi = 0.318309886183790671538f;
-
 // Mandelbulb (Listing "Mandelbulb distance", Eq. 1): w0 = c, dz = 1; each step
 // dz <- n r^(n-1) dz + 1 and w <- r^n (sin b sin a, cos b, sin b cos a) + c with
 // r = |w|, b = n acos(w.y / r) (y/r clamped to [-1, 1]), a = n atan2(w.x, w.z);
@@ -272,6 +273,19 @@ __device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
     o.a = p.x; o.b = p.y; o.c = p.z; o.d = 0.0f;
     o.m = dot3(p, p);
     o.dz = 1.0f;
+}
+
+// The listing's angles of w for the power n, in half-turns (x 1/pi):
+// b = n acos(u) with u = w.y / r clamped to [-1, 1], a = n atan2(w.x, w.z).
+// In half-turns sin and cos come from sincospif, which needs no range
+// reduction by pi; acospi and atan2pi (fr_math.cuh) return the angles in
+// half-turns directly.  Returns u.
+__device__ __forceinline__ float bulb_angles(float3 w, float r, float nf, float &b, float &a)
+{
+    const float u = fminf(fmaxf(quot(w.y, r), -1.0f), 1.0f);
+    b = mul(nf, acospi(u));
+    a = mul(nf, atan2pi(w.x, w.z));
+    return u;
 }
 
 // r^k for an integer 0 <= k < 16 by binary exponentiation (each product
@@ -309,13 +323,8 @@ __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
     o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
-        const float ct = fminf(fmaxf(dvd(o.b, r), -1.0f), 1.0f);
-        // the angles n acos(y/r) and n atan2(x, z) in half-turns (x n/pi), so
-        // that sin and cos come from sincospif: no range reduction by pi,
-        // fewer instructions and a shorter dependent chain than sincosf
-        const float nh = mul(nf, kInvPi);
-        const float b = mul(nh, acosf(ct));
-        const float a = mul(nh, atan2f(o.a, o.c));
+        float b, a;
+        bulb_angles(v3(o.a, o.b, o.c), r, nf, b, a);
         float sb, cb, sa, ca;
         sincospif(b, &sb, &cb);
         sincospif(a, &sa, &ca);
@@ -676,10 +685,8 @@ __device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, int n, f
             const float r = sqrtf(dot3(w, w));
             float3 P = v3(0.0f, 0.0f, 0.0f), dP = P;
             if (r > 0.0f) {
-                const float u = fminf(fmaxf(dvd(w.y, r), -1.0f), 1.0f);
-                const float nh = mul(nf, kInvPi);  // angles in half-turns, as bulb_step
-                const float b = mul(nh, acosf(u));
-                const float a = mul(nh, atan2f(w.x, w.z));
+                float b, a;
+                const float u = bulb_angles(w, r, nf, b, a);  // as bulb_step
                 float sb, cb, sa, ca;
                 sincospif(b, &sb, &cb);
                 sincospif(a, &sa, &ca);
