@@ -33,15 +33,15 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # everything included (orbit step, DE epilogue, march update, stencils, camera
 # ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
 # divided by the iterations counted on the same scene (Mandelbulb n = 8 at
-# 1920x1080: 8.532 G / 50.88 M = 167.7; Julia p = 2 at 256x256:
+# 1920x1080: 7.376 G / 50.88 M = 145.0; Julia p = 2 at 256x256:
 # 364.9 M / 10.27 M = 35.6; Mandelbulb powers 2..10 at 960x540, the same
 # scene and camera, one request each).  The degree-3 Julia figure is the
 # degree-2 one scaled by the ratio of their orbit-step arithmetic (28 / 24);
 # Mandelbulb powers 11..16 take the n = 10 figure.
 FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5,
-                  ("bulb", 2): 153.1, ("bulb", 3): 157.6, ("bulb", 4): 161.9, ("bulb", 5): 165.6,
-                  ("bulb", 6): 167.8, ("bulb", 7): 168.7, ("bulb", 8): 167.7, ("bulb", 9): 172.9,
-                  ("bulb", 10): 173.9}
+                  ("bulb", 2): 129.5, ("bulb", 3): 134.7, ("bulb", 4): 138.7, ("bulb", 5): 142.7,
+                  ("bulb", 6): 144.3, ("bulb", 7): 145.9, ("bulb", 8): 145.0, ("bulb", 9): 149.9,
+                  ("bulb", 10): 150.7}
 # The algorithmic count of the same work: the operations of the listings'
 # formulas as written, each math-library call (sqrt, pow, acos, atan2, sin,
 # cos, log) counted as one operation, nothing for the library's internals.
@@ -59,12 +59,12 @@ ALG_PER_DE = {"julia": 19, "bulb": 17}
 # configuration launches), from the ncu capture of the same command
 # (dram__bytes_read.sum + dram__bytes_write.sum); the frame's 16.6 MB of
 # stores are still in the 129 MB L2 when the kernel ends.
-TRAFFIC = {("bulb_1080p", "plain_kernel"): 46336 + 1024, ("bulb_1080p", "batch_plain_kernel"): 82432 + 0}
+TRAFFIC = {("bulb_1080p", "plain_kernel"): 44544 + 1024}
 # The kernel sources the two tables above were counted on (sha256 over these
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
 COUNTED_SOURCES = ("fr_device.cuh", "fr_math.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
-COUNTED_SHA = "7e6ad19bd05fa59fcc05b75ab5b573bcd7cdca9ef137d73c059dea41cc3f535b"
+COUNTED_SHA = "2a47c1048f7d7ba46713f0d22b038ba44a6b90baef8a0986c7f6d55fb2cbecac"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 
 

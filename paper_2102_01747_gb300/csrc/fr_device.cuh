@@ -277,9 +277,9 @@ __device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
 
 // The listing's angles of w for the power n, in half-turns (x 1/pi):
 // b = n acos(u) with u = w.y / r clamped to [-1, 1], a = n atan2(w.x, w.z).
-// In half-turns sin and cos come from sincospif, which needs no range
-// reduction by pi; acospi and atan2pi (fr_math.cuh) return the angles in
-// half-turns directly.  Returns u.
+// In half-turns sin and cos need no range reduction by pi (sincospi_own);
+// acospi and atan2pi return the angles in half-turns directly (all three in
+// fr_math.cuh).  Returns u.
 __device__ __forceinline__ float bulb_angles(float3 w, float r, float nf, float &b, float &a)
 {
     const float u = fminf(fmaxf(quot(w.y, r), -1.0f), 1.0f);
@@ -326,8 +326,8 @@ __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
         float b, a;
         bulb_angles(v3(o.a, o.b, o.c), r, nf, b, a);
         float sb, cb, sa, ca;
-        sincospif(b, &sb, &cb);
-        sincospif(a, &sa, &ca);
+        sincospi_own(b, &sb, &cb);
+        sincospi_own(a, &sa, &ca);
         const float rn = mul(rn1, r);  // r^n (the listing's pow(r, n))
         px = mul(rn, mul(sb, sa));
         py = mul(rn, cb);
@@ -688,8 +688,8 @@ __device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, int n, f
                 float b, a;
                 const float u = bulb_angles(w, r, nf, b, a);  // as bulb_step
                 float sb, cb, sa, ca;
-                sincospif(b, &sb, &cb);
-                sincospif(a, &sa, &ca);
+                sincospi_own(b, &sb, &cb);
+                sincospi_own(a, &sa, &ca);
                 const float rn1 = rpow_nm1(r, n);
                 const float rn = mul(rn1, r);
                 P = v3(mul(rn, mul(sb, sa)), mul(rn, cb), mul(rn, mul(sb, ca)));

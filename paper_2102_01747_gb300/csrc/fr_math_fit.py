@@ -3,8 +3,10 @@
 Each polynomial is a relative-error minimax fit found by the Remez exchange
 algorithm in 40-digit arithmetic (mpmath), then rounded to float:
 
-  atan(q) / (pi q) = P(s),  s = q^2 in [0, 1],     degree 8
-  asin(s) / (pi s) = Q(u),  u = s^2 in [0, 1/4],   degree 5
+  atan(q) / (pi q)        = P(s), s = q^2 in [0, 1],     degree 8
+  asin(s) / (pi s)        = Q(u), u = s^2 in [0, 1/4],   degree 5
+  sin(pi f) / f           = S(v), v = f^2 in [0, 1/16],  degree 3
+  (cos(pi f) - 1) / f^2   = C(v), v = f^2 in [0, 1/16],  degree 3
 
 The Remez exchange: start from Chebyshev extrema, solve the linear system
 p(x_i) + (-1)^i E f(x_i) = f(x_i) for the coefficients and the levelled error
@@ -59,6 +61,14 @@ def asin_over_pi(u):
     return mp.asin(mp.sqrt(u)) / (mp.pi * mp.sqrt(u)) if u > 0 else 1 / mp.pi
 
 
+def sin_pi_over_f(v):
+    return mp.sin(mp.pi * mp.sqrt(v)) / mp.sqrt(v) if v > 0 else mp.pi
+
+
+def cos_pi_m1_over_f2(v):
+    return (mp.cos(mp.pi * mp.sqrt(v)) - 1) / v if v > 0 else -mp.pi ** 2 / 2
+
+
 def to_float(x):
     import struct
     return struct.unpack("f", struct.pack("f", float(x)))[0]
@@ -66,7 +76,9 @@ def to_float(x):
 
 if __name__ == "__main__":
     for name, f, lo, hi, deg in (("atan2pi P(q^2)", atan_over_pi, 0, 1, 8),
-                                 ("acospi Q(s^2)", asin_over_pi, 0, 0.25, 5)):
+                                 ("acospi Q(s^2)", asin_over_pi, 0, 0.25, 5),
+                                 ("sincospi_own S(f^2)", sin_pi_over_f, 0, mp.mpf(1) / 16, 3),
+                                 ("sincospi_own C(f^2)", cos_pi_m1_over_f2, 0, mp.mpf(1) / 16, 3)):
         c, err = remez(f, lo, hi, deg)
         print("%s: degree %d, relative error %.3e before rounding" % (name, deg, float(err)))
         for x in c[::-1]:
