@@ -259,7 +259,9 @@ __device__ __forceinline__ void julia3_step(Orbit &o, const float4 c)
 
 __device__ __forceinline__ float julia_dist(const Orbit &o)
 {
-    return mul(mul(0.25f, logf(o.m)), sqrtf(dvd(o.m, o.dz)));
+    // (|z'|^2 can underflow to 0 only after |z| has, and m / 0 = inf is held
+    // finite for sqrt_own: the distance is then as large as float allows)
+    return mul(mul(0.25f, log_own(o.m)), sqrt_own(fminf(dvd(o.m, o.dz), 3.40282347e38f)));
 }
 
 // Mandelbulb (Listing "Mandelbulb distance", Eq. 1): w0 = c, dz = 1; each step
@@ -318,7 +320,7 @@ __device__ __forceinline__ float rpow_nm1(float r, int n)
 __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
 {
     const float nf = (float)n;
-    const float r = sqrtf(o.m);
+    const float r = sqrt_own(o.m);
     const float rn1 = rpow_nm1(r, n);  // r^(n-1) (the listing's pow(sqrt(m), n-1))
     o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
@@ -419,7 +421,9 @@ __device__ __forceinline__ void bulb_step_alg(Orbit &o, float3 cpt, int n)
 
 __device__ __forceinline__ float bulb_dist(const Orbit &o)
 {
-    return dvd(mul(mul(0.25f, logf(o.m)), sqrtf(o.m)), o.dz);
+    // dz >= 1; above 2^126 (it overflows to inf after ~12 steps at r ~ 2) the
+    // distance is below 1e-37 either way: dz is held at 2^126 for quot
+    return quot(mul(mul(0.25f, log_own(o.m)), sqrt_own(o.m)), fminf(o.dz, 8.507059e37f));
 }
 
 // whole-orbit DEs (one-ray-per-thread kernel); trips = orbit loop trips
@@ -682,7 +686,7 @@ __device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, int n, f
         i = 0;
         for (int k = 0; k < R.max_iter; k++) {
             i++;
-            const float r = sqrtf(dot3(w, w));
+            const float r = sqrt_own(dot3(w, w));
             float3 P = v3(0.0f, 0.0f, 0.0f), dP = P;
             if (r > 0.0f) {
                 float b, a;

@@ -31,7 +31,7 @@ __device__ float lcg_unit(uint64_t &s)
 }
 
 enum { kAtanOwn, kAtanLib, kAtanAbs, kAcosOwn, kAcosLib, kAcosAbs, kSinAbsOwn, kCosAbsOwn,
-       kSinAbsLib, kCosAbsLib, kQuot, kSlots };
+       kSinAbsLib, kCosAbsLib, kQuot, kSqrtOwn, kLogOwn, kLogLib, kSlots };
 
 __global__ void atan2_kernel(unsigned long long *m, long long n)
 {
@@ -83,6 +83,21 @@ __global__ void sincos_kernel(unsigned long long *m, long long n)
     }
 }
 
+__global__ void sqrt_log_kernel(unsigned long long *m, long long n)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint64_t s = 0x2545f4914f6cdd1dULL ^ (uint64_t)i;
+        // log-uniform over [2^-126, 2^20] and uniform over [1/2, 2] in turn
+        const float x = (i & 1) ? 0.5f + 1.5f * lcg_unit(s)
+                                : exp2f(-126.0f + 146.0f * lcg_unit(s));
+        keep_max(&m[kSqrtOwn], ulps(sqrt_own(x), sqrt((double)x)));
+        const double rl = log((double)x);
+        keep_max(&m[kLogOwn], ulps(log_own(x), rl));
+        keep_max(&m[kLogLib], ulps(logf(x), rl));
+    }
+}
+
 // special points, one thread
 __global__ void special_kernel(float *o)
 {
@@ -104,6 +119,12 @@ __global__ void special_kernel(float *o)
     sincospi_own(-1.5f, &s, &c);
     o[12] = s;
     o[13] = c;
+    o[14] = sqrt_own(0.0f);
+    o[15] = sqrt_own(4.0f);
+    o[16] = sqrt_own(1e-40f);
+    o[17] = log_own(1.0f);
+    o[18] = log_own(0.0f);
+    o[19] = log_own(2.0f);
 }
 
 int main()
@@ -111,7 +132,7 @@ int main()
     unsigned long long *m = nullptr;
     float *sp = nullptr;
     if (cudaMalloc(&m, kSlots * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&sp, 16 * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&sp, 20 * sizeof(float)) != cudaSuccess) {
         fprintf(stderr, "cudaMalloc failed\n");
         return 1;
     }
@@ -119,9 +140,10 @@ int main()
     atan2_kernel<<<152 * 8, 256>>>(m, 1LL << 27);
     acos_kernel<<<152 * 8, 256>>>(m, 1LL << 26);
     sincos_kernel<<<152 * 8, 256>>>(m, 1LL << 26);
+    sqrt_log_kernel<<<152 * 8, 256>>>(m, 1LL << 26);
     special_kernel<<<1, 1>>>(sp);
     unsigned long long h[kSlots];
-    float hs[14];
+    float hs[20];
     cudaMemcpy(h, m, sizeof h, cudaMemcpyDeviceToHost);
     cudaMemcpy(hs, sp, sizeof hs, cudaMemcpyDeviceToHost);
     const cudaError_t err = cudaDeviceSynchronize();
@@ -131,10 +153,11 @@ int main()
     }
     const char *names[kSlots] = {"atan2pi_ulp", "atan2f_ulp", "atan2pi_abs_e6", "acospi_ulp", "acosf_ulp",
                                  "acospi_abs_e6", "sinpi_abs_e6", "cospi_abs_e6", "sincospif_sin_abs_e6",
-                                 "sincospif_cos_abs_e6", "quot_ulp"};
+                                 "sincospif_cos_abs_e6", "quot_ulp", "sqrt_own_ulp", "log_own_ulp",
+                                 "logf_ulp"};
     for (int k = 0; k < kSlots; k++) printf("%s=%.6g ", names[k], (double)h[k] / 1e9);
     printf("special=");
-    for (int k = 0; k < 14; k++) printf("%s%.9g", k ? "," : "", hs[k]);
+    for (int k = 0; k < 20; k++) printf("%s%.9g", k ? "," : "", hs[k]);
     printf("\n");
     return 0;
 }

@@ -1,5 +1,6 @@
-"""The orbit step's own transcendental routines (fr_math.cuh: atan2pi, acospi,
-sincospi_own, quot) against double precision on the device: the error bounds
+"""The distance estimators' own elementary functions (fr_math.cuh: atan2pi,
+acospi, sincospi_own, quot, sqrt_own, log_own) against double precision on
+the device: the error bounds
 the header states, and the library routines they replaced measured beside
 them on the same arguments (tests/math_probe/math_probe.cu)."""
 import math
@@ -39,8 +40,12 @@ def test_math_routines_error_bounds():
     assert m["atan2pi_ulp"] <= m["atan2f_ulp"] + 0.5 and m["acospi_ulp"] <= m["acosf_ulp"] + 0.5, m
     # sin and cos of pi x on [-16, 16]
     assert m["sinpi_abs_e6"] <= 0.09 and m["cospi_abs_e6"] <= 0.09, m
-    assert m["quot_ulp"] <= 1.0, m
+    assert m["quot_ulp"] <= 1.0 and m["sqrt_own_ulp"] <= 1.0, m
+    assert m["log_own_ulp"] <= 2.0, m
     # atan2 of signed zeros as IEEE atan2 has them, exact axis and diagonal values
     assert sp[:10] == [0.0, -0.0, 1.0, -1.0, 0.5, 1.0, 0.25, 0.0, 1.0, 0.5], sp
     assert [math.copysign(1.0, v) for v in sp[:4]] == [1.0, -1.0, 1.0, -1.0], sp
     assert [abs(v) for v in sp[10:14]] == [0.0, 1.0, 1.0, 0.0], sp  # sin, cos of 8 pi and of -1.5 pi
+    # sqrt of 0, 4 and a subnormal (taken as 0); log of 1, 0 (taken as the smallest normal) and 2
+    assert sp[14:18] == [0.0, 2.0, 0.0, 0.0], sp
+    assert abs(sp[18] - math.log(2.0 ** -126)) < 1e-5 and abs(sp[19] - math.log(2.0)) < 1e-7, sp
