@@ -281,10 +281,11 @@ __device__ __forceinline__ void bulb_init(Orbit &o, float3 p)
 // b = n acos(u) with u = w.y / r clamped to [-1, 1], a = n atan2(w.x, w.z).
 // In half-turns sin and cos need no range reduction by pi (sincospi_own);
 // acospi and atan2pi return the angles in half-turns directly (all three in
-// fr_math.cuh).  Returns u.
-__device__ __forceinline__ float bulb_angles(float3 w, float r, float nf, float &b, float &a)
+// fr_math.cuh).  u is w.y times 1 / r (ir, from the seed that gave r, so the
+// angle does not wait for r).  Returns u.
+__device__ __forceinline__ float bulb_angles(float3 w, float ir, float nf, float &b, float &a)
 {
-    const float u = fminf(fmaxf(quot(w.y, r), -1.0f), 1.0f);
+    const float u = fminf(fmaxf(mul(w.y, ir), -1.0f), 1.0f);
     b = mul(nf, acospi(u));
     a = mul(nf, atan2pi(w.x, w.z));
     return u;
@@ -320,13 +321,14 @@ __device__ __forceinline__ float rpow_nm1(float r, int n)
 __device__ __forceinline__ void bulb_step(Orbit &o, float3 cpt, int n)
 {
     const float nf = (float)n;
-    const float r = sqrt_own(o.m);
+    float ir;
+    const float r = sqrt_rsqrt_own(o.m, ir);
     const float rn1 = rpow_nm1(r, n);  // r^(n-1) (the listing's pow(sqrt(m), n-1))
     o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
         float b, a;
-        bulb_angles(v3(o.a, o.b, o.c), r, nf, b, a);
+        bulb_angles(v3(o.a, o.b, o.c), ir, nf, b, a);
         float sb, cb, sa, ca;
         sincospi_own(b, &sb, &cb);
         sincospi_own(a, &sa, &ca);
@@ -384,19 +386,19 @@ __device__ __forceinline__ void cpow8(float c, float s, float &rc, float &rs)
 __device__ __forceinline__ void bulb_step_alg(Orbit &o, float3 cpt, int n)
 {
     const float nf = (float)n;
-    const float r = sqrtf(o.m);
+    float ir;
+    const float r = sqrt_rsqrt_own(o.m, ir);  // r and 1 / r
     const float rn1 = rpow_nm1(r, n);
     o.dz = fmaf(mul(nf, rn1), o.dz, 1.0f);
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     if (r > 0.0f) {
         const float rho2 = fmaf(o.c, o.c, mul(o.a, o.a));
-        const float ir = __frcp_rn(r);
         const float cb0 = fminf(fmaxf(mul(o.b, ir), -1.0f), 1.0f);
-        const float rho = sqrtf(rho2);
+        float irho;
+        const float rho = sqrt_rsqrt_own(rho2, irho);  // rho and 1 / rho
         const float sb0 = mul(rho, ir);
         float ca0 = 1.0f, sa0 = 0.0f;
         if (rho > 0.0f) {
-            const float irho = __frcp_rn(rho);
             ca0 = mul(o.c, irho);
             sa0 = mul(o.a, irho);
         }
@@ -686,11 +688,12 @@ __device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, int n, f
         i = 0;
         for (int k = 0; k < R.max_iter; k++) {
             i++;
-            const float r = sqrt_own(dot3(w, w));
+            float ir;
+            const float r = sqrt_rsqrt_own(dot3(w, w), ir);
             float3 P = v3(0.0f, 0.0f, 0.0f), dP = P;
             if (r > 0.0f) {
                 float b, a;
-                const float u = bulb_angles(w, r, nf, b, a);  // as bulb_step
+                const float u = bulb_angles(w, ir, nf, b, a);  // as bulb_step
                 float sb, cb, sa, ca;
                 sincospi_own(b, &sb, &cb);
                 sincospi_own(a, &sa, &ca);

@@ -31,7 +31,7 @@ __device__ float lcg_unit(uint64_t &s)
 }
 
 enum { kAtanOwn, kAtanLib, kAtanAbs, kAcosOwn, kAcosLib, kAcosAbs, kSinAbsOwn, kCosAbsOwn,
-       kSinAbsLib, kCosAbsLib, kQuot, kSqrtOwn, kLogOwn, kLogLib, kSlots };
+       kSinAbsLib, kCosAbsLib, kQuot, kSqrtOwn, kLogOwn, kLogLib, kRsqrtOwn, kSlots };
 
 __global__ void atan2_kernel(unsigned long long *m, long long n)
 {
@@ -92,6 +92,10 @@ __global__ void sqrt_log_kernel(unsigned long long *m, long long n)
         const float x = (i & 1) ? 0.5f + 1.5f * lcg_unit(s)
                                 : exp2f(-126.0f + 146.0f * lcg_unit(s));
         keep_max(&m[kSqrtOwn], ulps(sqrt_own(x), sqrt((double)x)));
+        float inv;
+        const float r2 = sqrt_rsqrt_own(x, inv);
+        keep_max(&m[kRsqrtOwn], ulps(inv, 1.0 / sqrt((double)x)));
+        if (r2 != sqrt_own(x)) keep_max(&m[kRsqrtOwn], 1e9);  // the same bits as sqrt_own
         const double rl = log((double)x);
         keep_max(&m[kLogOwn], ulps(log_own(x), rl));
         keep_max(&m[kLogLib], ulps(logf(x), rl));
@@ -154,7 +158,7 @@ int main()
     const char *names[kSlots] = {"atan2pi_ulp", "atan2f_ulp", "atan2pi_abs_e6", "acospi_ulp", "acosf_ulp",
                                  "acospi_abs_e6", "sinpi_abs_e6", "cospi_abs_e6", "sincospif_sin_abs_e6",
                                  "sincospif_cos_abs_e6", "quot_ulp", "sqrt_own_ulp", "log_own_ulp",
-                                 "logf_ulp"};
+                                 "logf_ulp", "rsqrt_own_ulp"};
     for (int k = 0; k < kSlots; k++) printf("%s=%.6g ", names[k], (double)h[k] / 1e9);
     printf("special=");
     for (int k = 0; k < 20; k++) printf("%s%.9g", k ? "," : "", hs[k]);

@@ -1,5 +1,5 @@
 """The distance estimators' own elementary functions (fr_math.cuh: atan2pi,
-acospi, sincospi_own, quot, sqrt_own, log_own) against double precision on
+acospi, sincospi_own, quot, sqrt_own, sqrt_rsqrt_own, log_own) against double precision on
 the device: the error bounds
 the header states, and the library routines they replaced measured beside
 them on the same arguments (tests/math_probe/math_probe.cu)."""
@@ -41,7 +41,7 @@ def test_math_routines_error_bounds():
     # sin and cos of pi x on [-16, 16]
     assert m["sinpi_abs_e6"] <= 0.09 and m["cospi_abs_e6"] <= 0.09, m
     assert m["quot_ulp"] <= 1.0 and m["sqrt_own_ulp"] <= 1.0, m
-    assert m["log_own_ulp"] <= 2.0, m
+    assert m["log_own_ulp"] <= 2.0 and m["rsqrt_own_ulp"] <= 1.5, m
     # atan2 of signed zeros as IEEE atan2 has them, exact axis and diagonal values
     assert sp[:10] == [0.0, -0.0, 1.0, -1.0, 0.5, 1.0, 0.25, 0.0, 1.0, 0.5], sp
     assert [math.copysign(1.0, v) for v in sp[:4]] == [1.0, -1.0, 1.0, -1.0], sp
