@@ -33,15 +33,15 @@ from paper_2102_01747_gb300 import workloads as W  # noqa: E402
 # everything included (orbit step, DE epilogue, march update, stencils, camera
 # ray, shading): ncu's SASS counters 2*FFMA + FADD + FMUL over one launch
 # divided by the iterations counted on the same scene (Mandelbulb n = 8 at
-# 1920x1080: 7.376 G / 50.88 M = 145.0; Julia p = 2 at 256x256:
-# 364.9 M / 10.27 M = 35.6; Mandelbulb powers 2..10 at 960x540, the same
-# scene and camera, one request each).  The degree-3 Julia figure is the
-# degree-2 one scaled by the ratio of their orbit-step arithmetic (28 / 24);
-# Mandelbulb powers 11..16 take the n = 10 figure.
-FLOPS_PER_ITER = {("julia", 2): 35.6, ("julia", 3): 41.5,
-                  ("bulb", 2): 129.5, ("bulb", 3): 134.7, ("bulb", 4): 138.7, ("bulb", 5): 142.7,
-                  ("bulb", 6): 144.3, ("bulb", 7): 145.9, ("bulb", 8): 145.0, ("bulb", 9): 149.9,
-                  ("bulb", 10): 150.7}
+# 1920x1080, the orbit loop unrolled 4 times: 7.363 G / 50.88 M = 144.7;
+# Julia p = 2 at 256x256: 356.3 M / 10.27 M = 34.7; Mandelbulb powers 2..10
+# at 960x540, the same scene and camera, one request each).  The degree-3
+# Julia figure is the degree-2 one scaled by the ratio of their orbit-step
+# arithmetic (28 / 24); Mandelbulb powers 11..16 take the n = 10 figure.
+FLOPS_PER_ITER = {("julia", 2): 34.7, ("julia", 3): 40.5,
+                  ("bulb", 2): 131.0, ("bulb", 3): 135.7, ("bulb", 4): 139.2, ("bulb", 5): 142.8,
+                  ("bulb", 6): 144.2, ("bulb", 7): 145.7, ("bulb", 8): 144.7, ("bulb", 9): 149.2,
+                  ("bulb", 10): 150.0}
 # The algorithmic count of the same work: the operations of the listings'
 # formulas as written, each math-library call (sqrt, pow, acos, atan2, sin,
 # cos, log) counted as one operation, nothing for the library's internals.
@@ -59,12 +59,12 @@ ALG_PER_DE = {"julia": 19, "bulb": 17}
 # configuration launches), from the ncu capture of the same command
 # (dram__bytes_read.sum + dram__bytes_write.sum); the frame's 16.6 MB of
 # stores are still in the 129 MB L2 when the kernel ends.
-TRAFFIC = {("bulb_1080p", "plain_kernel"): 44544 + 1024}
+TRAFFIC = {("bulb_1080p", "plain_kernel"): 58880 + 512}
 # The kernel sources the two tables above were counted on (sha256 over these
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
 COUNTED_SOURCES = ("fr_device.cuh", "fr_math.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
-COUNTED_SHA = "2a47c1048f7d7ba46713f0d22b038ba44a6b90baef8a0986c7f6d55fb2cbecac"
+COUNTED_SHA = "5631fd494ec656a38b15afcff96dd9eae8a36797faa17a019436e7742f6f6ae0"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 
 
@@ -435,6 +435,8 @@ def measure(args, torch, api, F, scenes, path, env, steps, warmup, clk_index=Non
             del space["tile_order"]
         if args.sample_lanes is not None:
             del space["sample_lanes"]
+        if args.unroll is not None:
+            del space["plain_unroll"]
         r = autotune.tune(scenes, reps=tune_reps, space=space)  # untimed search over the launch shape
         tuning = {"config": r["config"], "search_ms": r["ms"], "trials": len(r["trials"])}
     elif tune and path == "plain" and len(scenes) == 1:
@@ -447,6 +449,8 @@ def measure(args, torch, api, F, scenes, path, env, steps, warmup, clk_index=Non
             del space["single_kernel"]
         if args.sample_lanes is not None:
             del space["sample_lanes"]
+        if args.unroll is not None:
+            del space["plain_unroll"]
         r = autotune.tune_single(scenes[0], reps=max(tune_reps, 3), space=space, start_kernel=args.single_kernel)
         tuning = {"config": r["config"], "search_ms": r["ms"], "trials": len(r["trials"]),
                   "trial_ms": [[{k: t[k] for k in space}, round(t["ms"], 4)] for t in r["trials"]]}
@@ -624,6 +628,9 @@ def main():
                     help="fix fr_render_batch's schedule (1 one-ray-per-thread kernel over all "
                          "tiles, 2 persistent warps taking tiles from a queue, 0 persistent lane "
                          "state machine); the autotuner then keeps it")
+    ap.add_argument("--unroll", type=int, choices=[1, 2, 4], default=None,
+                    help="fix the orbit-loop unroll depth of the one-ray-per-thread kernels "
+                         "(the batch kernels take 1 or 2); the autotuner then keeps it")
     ap.add_argument("--sample-lanes", type=int, choices=[0, 1], default=None,
                     help="fix where a pixel's 2, 4 or 8 samples run (1 adjacent lanes, 0 in turn on "
                          "one lane); the autotuner then keeps it")
@@ -655,8 +662,10 @@ def main():
     B.build()
     F.load()
     if (args.batch_kernel is not None or args.tile_order is not None or args.single_kernel is not None
-            or args.sample_lanes is not None):
+            or args.sample_lanes is not None or args.unroll is not None):
         t = F.fr_get_tuning()
+        if args.unroll is not None:
+            t.plain_unroll = args.unroll
         if args.sample_lanes is not None:
             t.sample_lanes = args.sample_lanes
         if args.batch_kernel is not None:

@@ -4,6 +4,7 @@ For fr_render_batch (tune):
   batch_kernel       1 one-ray-per-thread kernel over all tiles, 2 persistent warps taking the
                      tiles from a queue, 0 persistent lane state machine
   plain_block        threads per CTA of the one-ray-per-thread batch kernel
+  plain_unroll       orbit-loop unroll depth of the one-ray-per-thread batch kernels (1 or 2)
   tile_order         order of the tiles in the launch (rows, columns, rows upward)
   sample_lanes       requests with 2, 4 or 8 samples: their samples on adjacent lanes (1) or
                      in turn on one lane (0)
@@ -35,6 +36,7 @@ from . import api
 SPACE = {
     "batch_kernel": (1, 2, 0),
     "plain_block": (32, 64, 128, 256),
+    "plain_unroll": (1, 2),
     "tile_order": (0, 1, 2),
     "sample_lanes": (1, 0),
     "persist_block": (64, 128, 256),
@@ -102,7 +104,7 @@ def _in_use(knob: str, cfg: dict) -> bool:
     """Whether `knob` changes what fr_render_batch launches under `cfg`."""
     if knob in PERSIST_KNOBS:
         return cfg.get("batch_kernel", 0) == 0
-    if knob in ("plain_block", "tile_order", "sample_lanes"):
+    if knob in ("plain_block", "plain_unroll", "tile_order", "sample_lanes"):
         return cfg.get("batch_kernel", 0) in (1, 2)
     return True
 
