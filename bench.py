@@ -64,7 +64,7 @@ TRAFFIC = {("bulb_1080p", "plain_kernel"): 58880 + 512}
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
 COUNTED_SOURCES = ("fr_device.cuh", "fr_math.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
-COUNTED_SHA = "5631fd494ec656a38b15afcff96dd9eae8a36797faa17a019436e7742f6f6ae0"
+COUNTED_SHA = "6c27831d09862493a4bfc5f05fcc626cda0cebf76b38930da2fa5275320250dd"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 
 

@@ -49,7 +49,10 @@ def remez(f, a, b, deg, iters=30, grid=4000):
             alt.pop(0 if abs(ev[alt[0]]) < abs(ev[alt[-1]]) else -1)
         if len(alt) < n:
             break
-        xs = [pts[k] for k in alt]
+        new = [pts[k] for k in alt]
+        if new == xs:  # the reference has settled: the next solve gives the same polynomial
+            break
+        xs = new
     return c, max(abs(e) for e in ev)
 
 
