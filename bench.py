@@ -114,6 +114,10 @@ def workload(name: str, rank: int = 0):
         return [W.stress_bulb_4k(60 + rank)], "Mandelbulb n=8 3840x2160 4 spp, iteration cap 12 (frame 60)"
     if name == "stress_julia_4k":
         return [W.stress_julia_4k()], "quaternion Julia 3840x2160 with shadow rays"
+    if name == "bulb_1080p_analytic":
+        return [dict(W.bulb_1080p(10 + rank), normal_mode="analytic")], (
+            "Mandelbulb n=8 1920x1080 (bulb_1080p scene), analytic normal (Sec. 2) instead of the tetrahedral "
+            "stencil, frame %d" % (10 + rank))
     if name == "julia_4k_analytic":
         return [dict(W.stress_julia_4k(), normal_mode="analytic")], (
             "quaternion Julia 3840x2160 with shadow rays, analytic normal (Sec. 2) instead of central differences")

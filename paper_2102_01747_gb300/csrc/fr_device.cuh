@@ -701,11 +701,16 @@ __device__ __forceinline__ float3 bulb_analytic_normal(const DevReq &R, int n, f
                 const float rn = mul(rn1, r);
                 P = v3(mul(rn, mul(sb, sa)), mul(rn, cb), mul(rn, mul(sb, ca)));
                 const float rho2 = fmaf(w.z, w.z, mul(w.x, w.x));
-                const float su = sqrtf(fmaxf(fmaf(-u, u, 1.0f), 0.0f));
-                const float dr = dvd(dot3(w, d), r);
-                const float du = dvd(fmaf(-w.y, dr, mul(d.y, r)), mul(r, r));
-                const float db = su > 0.0f ? dvd(mul(-nf, du), su) : 0.0f;
-                const float da = rho2 > 0.0f ? dvd(mul(nf, fmaf(w.z, d.x, -mul(w.x, d.z))), rho2) : 0.0f;
+                // the divisions by r, r^2, sqrt(1 - u^2) and rho^2 as products with the
+                // reciprocals (ir from the step's seed; 1/sqrt(1 - u^2) and 1/rho from
+                // one seed each; zero below the normal range, on the polar axis)
+                float isu, irho;
+                const float su = sqrt_rsqrt_own(fmaxf(fmaf(-u, u, 1.0f), 0.0f), isu);
+                const float rho = sqrt_rsqrt_own(rho2, irho);
+                const float dr = mul(dot3(w, d), ir);
+                const float du = mul(mul(fmaf(-w.y, dr, mul(d.y, r)), ir), ir);
+                const float db = su > 0.0f ? mul(mul(-nf, du), isu) : 0.0f;
+                const float da = rho > 0.0f ? mul(mul(mul(nf, fmaf(w.z, d.x, -mul(w.x, d.z))), irho), irho) : 0.0f;
                 const float drn = mul(mul(nf, rn1), dr);
                 const float cbdb = mul(cb, db), sbda = mul(sb, da);
                 dP = v3(fmaf(drn, mul(sb, sa), mul(rn, fmaf(cbdb, sa, mul(ca, sbda)))),
