@@ -64,7 +64,7 @@ TRAFFIC = {("bulb_1080p", "plain_kernel"): 58880 + 512}
 # files in this order): when the sources change, the bench reports the
 # figures as stale and the traffic as null until they are counted again.
 COUNTED_SOURCES = ("fr_device.cuh", "fr_math.cuh", "fr_trace.cuh", "fr_plain.cuh", "fr_plain.cu", "fr_launch.h")
-COUNTED_SHA = "6c27831d09862493a4bfc5f05fcc626cda0cebf76b38930da2fa5275320250dd"
+COUNTED_SHA = "273055e64402ef6e83b575aa52c654ab07f46c72ffc51245c32c84c13e18737b"
 FP32_LANES_PER_SM = 128  # FFMA lanes per SM (4 sub-partitions x 32), checked by the FFMA probe
 
 
