@@ -113,3 +113,38 @@ def test_random_scenes_as_one_batch(api, batch_kernel):
         F.fr_set_tuning(old)
     for k, (a, b) in enumerate(zip(singles, batch)):
         assert torch.equal(a["rgba8"], b["rgba8"]) and torch.equal(a["depth"], b["depth"]), k
+
+
+SWEEP = int(os.environ.get("FR_SWEEP_SCENES", "0"))
+
+
+@pytest.mark.skipif(SWEEP <= 0, reason="set FR_SWEEP_SCENES=N to render N random scenes (400 in the design notes)")
+def test_random_scene_sweep(api, orc):
+    """FR_SWEEP_SCENES seeded random scenes (seeds 1000, 1001, ...; the first 40
+    are the ones above) against the float oracle.  At least 99 % meet the
+    parity bar.  On every other scene hits and depths still meet it, only the
+    colour bar is missed, and the float oracle's own colours agree with the
+    double oracle's to within half a percent of that bar (the scene is
+    ill-conditioned in float, e.g. a sharp Phong highlight)."""
+    import torch
+
+    ok, misses = 0, []
+    for i in range(SWEEP):
+        s = random_scene(np.random.default_rng(1000 + i))
+        out = api.render(s, rgba8=True, depth=True)
+        torch.cuda.synchronize()
+        o = orc.render(s, precision="f32", threads=THREADS)
+        res = compare(_np(out["rgba8"]), _np(out["depth"]), o["rgba8"], o["depth"])
+        if res["ok"]:
+            ok += 1
+            continue
+        o64 = orc.render(s, precision="f64", threads=THREADS)
+        ref = compare(o["rgba8"], o["depth"], o64["rgba8"], o64["depth"])
+        misses.append((i, res, ref))
+    print("random scenes within the parity bar: %d / %d" % (ok, SWEEP))
+    for i, res, ref in misses:
+        print("scene", i, "GPU vs float oracle", res, "float vs double oracle", ref)
+    assert ok >= 0.99 * SWEEP, misses
+    for i, res, ref in misses:
+        assert res["hit_agree"] >= 0.995 and res["depth_ok"] >= 0.99, (i, res)
+        assert ref["rgb_ok"] < 0.995, (i, res, ref)
