@@ -1,9 +1,9 @@
 // fr_static.cu -- fr_render_batch_static: the batched render without a
 // caller-provided workspace, for callers that cannot allocate device memory.
 //
-// The persistent schedule (batch_kernel 0) needs one 256-byte queue head per
-// launch of up to 64 requests.  fr_render_batch takes that scratch from the
-// caller whichever schedule runs; this entry
+// The persistent schedules (batch_kernel 2, the default, and 0) need one
+// 256-byte queue head per launch of up to 64 requests.  fr_render_batch takes
+// that scratch from the caller whichever schedule runs; this entry
 // point takes it from a file-scope __device__ array instead, sized for the
 // largest batch fr_render_batch accepts (4096 requests = 64 launches = 16 KB).
 // Every GPU that loads the library holds the array until the process exits.
@@ -86,7 +86,7 @@ FR_API fr_status fr_render_batch_static(const fr_request *reqs, int32_t n_reqs, 
             e = cudaGetSymbolAddress(&ws, g_static_ws);
             if (e != cudaSuccess || !ws) {
                 cudaGetLastError();  // leave no error behind for the next launch check
-            snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+                snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
                 return fr::set_error(FR_ECUDA, msg);
             }
             g_static_addr[dev] = ws;
