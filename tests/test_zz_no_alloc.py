@@ -6,9 +6,10 @@ per launch of up to 64 requests, lives in a fixed array inside the library.
 
 Called through the C ABI twice in a row, it must give the same images, bit
 for bit, as fr_render_batch given a caller workspace.  The persistent
-schedules (batch_kernel 0 and 2) read the queue heads, so they run here with
-130 small requests: three launches, which use three different slots of the
-array.  The one-ray-per-thread schedule (the default) is checked too.
+schedules (batch_kernel 2, the default, and 0) read the queue heads, so they
+run here with 130 small requests: three launches, which use three different
+slots of the array.  The grid schedule (batch_kernel 1), which reads no queue
+head, is checked too.
 This file sorts last, so a stop-at-first-failure run has already run every
 other test."""
 import numpy as np
