@@ -548,10 +548,50 @@ def measure_gradient(args, torch, api, F, scene, steps, warmup):
             "clocks": clk, "width": s["camera"]["width"], "height": s["camera"]["height"]}
 
 
+def cpu_gradient_baseline(scene, budget_s: float = 10.0):
+    """The oracle's double-precision gradient (forward-mode dual numbers, the
+    march included) of the same scene and a fixed random cotangent, on all host
+    cores, over every stride-th pixel (the stride grown until the sample takes
+    about budget_s / 2); reported as whole-image gradients per second."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n = scene["camera"]["width"] * scene["camera"]["height"]
+    rng = np.random.default_rng(W.BASE_SEED)
+    d_rgba = rng.standard_normal((n, 4))
+    d_depth = 0.3 * rng.standard_normal(n)
+    stride = 64
+    while True:
+        mask = np.zeros(n, np.uint8)
+        mask[::stride] = 1
+        t0 = time.perf_counter()
+        oracle.julia_grad(scene, d_rgba, d_depth, mask=mask, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s / 4 or stride == 1:
+            break
+        stride = max(1, int(stride * dt / (budget_s / 2)) if dt > 0 else 1)
+    reps = 1
+    while dt < budget_s / 2 and reps < 10:
+        t0 = time.perf_counter()
+        oracle.julia_grad(scene, d_rgba, d_depth, mask=mask, threads=threads)
+        dt += time.perf_counter() - t0
+        reps += 1
+    frac = float(mask.sum()) / n
+    return {"value": reps * frac / dt, "unit": "grad/s", "cores": threads, "kind": "oracle",
+            "sample": "%s of the image, %d pass%s, %.1f s (double precision, dual numbers)" % (
+                _stride_words(stride), reps, "" if reps == 1 else "es", dt)}
+
+
 def run_gradient(args, torch, api, F, scenes, desc, rank, world):
     g = measure_gradient(args, torch, api, F, scenes[0], args.steps, args.warmup)
     if rank != 0:
         return
+    extra = {}
+    if world == 1 and not args.no_cpu_baseline:
+        extra["cpu_baseline"] = cpu_gradient_baseline(scenes[0])
     print(json.dumps({
         "metric": "grad/s", "value": g["value"], "unit": "grad/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": g["ms_per_step"],
@@ -559,7 +599,7 @@ def run_gradient(args, torch, api, F, scenes, desc, rank, world):
         "data": "synthetic", "config": {"workload": desc, "width": g["width"], "height": g["height"],
                                         "l2": "flushed between timed steps (256 MB write)"},
         "forward_ms": g["forward_ms"], "fd_grad_per_s": g["fd_grad_per_s"], "speedup_vs_fd": g["speedup_vs_fd"],
-        "e2e": g["e2e"], "gpu_launches": 2 * args.steps, "clocks": g["clocks"],
+        "e2e": g["e2e"], "gpu_launches": 2 * args.steps, "clocks": g["clocks"], **extra,
     }))
 
 
